@@ -1,0 +1,269 @@
+/*
+ * FP64 reference decoder for syndrome-based flooding sum-product belief
+ * propagation (BP) on an LDPC / MET-LDPC Tanner graph.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA decoder is
+ * checked against.  Only the test suite, the package's smoke check and the
+ * benchmark's CPU-baseline leg may load it; the decoder never calls it, and
+ * it shares no code, header or constant with the decoder.
+ *
+ * It follows the paper's Methods section ("Belief propagation decoding
+ * algorithm of LDPC code", Steps 1-5, Eqs. 1-5) step by step, in the
+ * log-likelihood-ratio (LLR) domain that the closing paragraph of that
+ * section recommends, with these readings of points the paper leaves open:
+ *
+ *   - LLR convention: L = ln p(x=0)/p(x=1); for the BIAWGN observation
+ *     y = (1-2x) + sigma z this is L = 2y/sigma^2.  The hard decision of
+ *     Step 5 ("c_i = 1 iff q_i > 1" in the ratio q(1)/q(0)) is x = 1 iff L < 0,
+ *     and L = 0 decides 0.
+ *   - Eqs. 2-3 do not show Bob's syndrome although Step 1 sends it and Step 5
+ *     compares against it: the check-to-variable message of check j carries
+ *     the factor (1 - 2 s_j).
+ *   - One iteration is a check update (Step 3) followed by a variable update
+ *     (Step 4); the channel values feed the first check update.  The
+ *     syndrome comparison (Step 5) happens after each iteration, so with
+ *     early termination at least one iteration runs.
+ *   - Clamps: channel LLRs, variable-to-check messages q and check-to-variable
+ *     messages r are limited to [-LMAX, LMAX] (LMAX = 25 by default), and
+ *     every argument of phi(x) = -ln tanh(x/2) is limited to
+ *     [phi(LMAX), LMAX], the interval phi maps onto itself.  The posterior of
+ *     Eq. 5 is not clamped.
+ *   - Eq. 5 writes q_ij^0 where the channel term of VN i is meant.
+ *
+ * Per iteration (Eqs. 2-5 in the LLR domain, flooding schedule, full graph,
+ * degree-1 VNs updated like every other VN):
+ *   q_{v->c} = clamp( Lch(v) + sum_{c' in C_v \ c} r_{c'->v} )           (Eq. 4)
+ *   r_{c->v} = clamp( (1-2 s_c) prod_{v' in R_c \ v} sgn q_{v'->c}
+ *                     * phi( sum_{v' in R_c \ v} phi(|q_{v'->c}|) ) )     (Eqs. 2-3)
+ *   L_v      = Lch(v) + sum_{c in C_v} r_{c->v},   xhat_v = [L_v < 0]    (Eq. 5)
+ * The leave-one-out sums are formed directly over the other edges (no
+ * total-minus-own shortcut).
+ *
+ * Also: weighted BP (a per-(iteration, edge type) scale on every
+ * variable-to-check message) and its exact reverse-mode gradient, used to
+ * check the decoder's adjoint.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL (-1)
+#define ORACLE_ENOMEM (-2)
+
+/* phi(x) = -ln tanh(x/2) = ln((e^x + 1)/(e^x - 1)) = log1p(2/expm1(x)), x > 0.
+ * The last form keeps full relative precision at both ends of (0, inf). */
+double oracle_phi(double x) { return log1p(2.0 / expm1(x)); }
+
+static double clampd(double x, double lo, double hi) {
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
+typedef struct {
+    int32_t n_vn, n_cn;
+    int64_t n_edges;
+    const int32_t *edge_vn, *edge_cn;
+    int64_t *cptr;   /* [n_cn+1]: edges of check c are cedge[cptr[c]..cptr[c+1]) */
+    int64_t *cedge;
+    int64_t *vptr;   /* [n_vn+1]: edges of VN v are vedge[vptr[v]..vptr[v+1]) */
+    int64_t *vedge;
+} adjacency;
+
+static void adj_free(adjacency *a) {
+    free(a->cptr); free(a->cedge); free(a->vptr); free(a->vedge);
+}
+
+static int adj_build(adjacency *a, int32_t n_vn, int32_t n_cn, int64_t n_edges,
+                     const int32_t *edge_vn, const int32_t *edge_cn) {
+    memset(a, 0, sizeof *a);
+    a->n_vn = n_vn; a->n_cn = n_cn; a->n_edges = n_edges;
+    a->edge_vn = edge_vn; a->edge_cn = edge_cn;
+    for (int64_t e = 0; e < n_edges; ++e)
+        if (edge_vn[e] < 0 || edge_vn[e] >= n_vn || edge_cn[e] < 0 || edge_cn[e] >= n_cn)
+            return ORACLE_EINVAL;
+    a->cptr = calloc((size_t)n_cn + 1, sizeof(int64_t));
+    a->vptr = calloc((size_t)n_vn + 1, sizeof(int64_t));
+    a->cedge = malloc(sizeof(int64_t) * (size_t)(n_edges > 0 ? n_edges : 1));
+    a->vedge = malloc(sizeof(int64_t) * (size_t)(n_edges > 0 ? n_edges : 1));
+    if (!a->cptr || !a->vptr || !a->cedge || !a->vedge) { adj_free(a); return ORACLE_ENOMEM; }
+    for (int64_t e = 0; e < n_edges; ++e) { a->cptr[edge_cn[e] + 1]++; a->vptr[edge_vn[e] + 1]++; }
+    for (int32_t c = 0; c < n_cn; ++c) a->cptr[c + 1] += a->cptr[c];
+    for (int32_t v = 0; v < n_vn; ++v) a->vptr[v + 1] += a->vptr[v];
+    int64_t *cfill = malloc(sizeof(int64_t) * ((size_t)n_cn + 1));
+    int64_t *vfill = malloc(sizeof(int64_t) * ((size_t)n_vn + 1));
+    if (!cfill || !vfill) { free(cfill); free(vfill); adj_free(a); return ORACLE_ENOMEM; }
+    memcpy(cfill, a->cptr, sizeof(int64_t) * ((size_t)n_cn + 1));
+    memcpy(vfill, a->vptr, sizeof(int64_t) * ((size_t)n_vn + 1));
+    for (int64_t e = 0; e < n_edges; ++e) {
+        a->cedge[cfill[edge_cn[e]]++] = e;
+        a->vedge[vfill[edge_vn[e]]++] = e;
+    }
+    free(cfill); free(vfill);
+    return ORACLE_OK;
+}
+
+/* Step 5: does the hard decision satisfy every check, H xhat = s (mod 2)? */
+static int syndrome_ok(const adjacency *a, const uint8_t *xhat, const uint8_t *s) {
+    for (int32_t c = 0; c < a->n_cn; ++c) {
+        int parity = s[c] & 1;
+        for (int64_t k = a->cptr[c]; k < a->cptr[c + 1]; ++k)
+            parity ^= xhat[a->edge_vn[a->cedge[k]]];
+        if (parity) return 0;
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Plain BP, one codeword.                                                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    const adjacency *a;
+    const double *llr;       /* [batch][n_vn] */
+    const uint8_t *syn;      /* [batch][n_cn] */
+    int32_t batch, max_iters, early_term;
+    double lmax;
+    double *post;            /* [batch][n_vn] or NULL */
+    uint8_t *bits;           /* [batch][n_vn] */
+    uint8_t *converged;      /* [batch] */
+    int32_t *iters_used;     /* [batch] */
+    int next;                /* work counter (atomic) */
+    int status;
+} decode_job;
+
+static int decode_one(const decode_job *J, int b) {
+    const adjacency *a = J->a;
+    const int32_t n = a->n_vn;
+    const int64_t E = a->n_edges;
+    const double lmax = J->lmax;
+    const double amin = oracle_phi(lmax);     /* phi maps [amin, lmax] onto itself */
+    const double *llr = J->llr + (size_t)b * n;
+    const uint8_t *s = J->syn + (size_t)b * a->n_cn;
+    double *Lch = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *L = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *q = malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    double *r = malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    double *phiq = malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    uint8_t *xhat = malloc((size_t)(n > 0 ? n : 1));
+    if (!Lch || !L || !q || !r || !phiq || !xhat) {
+        free(Lch); free(L); free(q); free(r); free(phiq); free(xhat);
+        return ORACLE_ENOMEM;
+    }
+    /* Step 2 / Eq. 1: channel values; no check message has been sent yet. */
+    for (int32_t v = 0; v < n; ++v) {
+        Lch[v] = clampd(llr[v], -lmax, lmax);
+        L[v] = Lch[v];
+        xhat[v] = L[v] < 0.0;
+    }
+    for (int64_t e = 0; e < E; ++e) r[e] = 0.0;
+
+    int used = 0, conv = 0;
+    for (int l = 1; l <= J->max_iters; ++l) {
+        /* Eq. 4: variable-to-check messages from the previous iteration's r. */
+        for (int32_t v = 0; v < n; ++v) {
+            for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) {
+                double acc = Lch[v];
+                for (int64_t k2 = a->vptr[v]; k2 < a->vptr[v + 1]; ++k2)
+                    if (k2 != k) acc += r[a->vedge[k2]];
+                q[a->vedge[k]] = clampd(acc, -lmax, lmax);
+            }
+        }
+        /* Eqs. 2-3 with the syndrome sign: check-to-variable messages. */
+        for (int64_t e = 0; e < E; ++e) phiq[e] = oracle_phi(clampd(fabs(q[e]), amin, lmax));
+        for (int32_t c = 0; c < a->n_cn; ++c) {
+            for (int64_t k = a->cptr[c]; k < a->cptr[c + 1]; ++k) {
+                double sgn = (s[c] & 1) ? -1.0 : 1.0;
+                double sum = 0.0;
+                for (int64_t k2 = a->cptr[c]; k2 < a->cptr[c + 1]; ++k2) {
+                    if (k2 == k) continue;
+                    int64_t e2 = a->cedge[k2];
+                    if (q[e2] < 0.0) sgn = -sgn;
+                    sum += phiq[e2];
+                }
+                double mag = oracle_phi(clampd(sum, amin, lmax));
+                r[a->cedge[k]] = clampd(sgn * mag, -lmax, lmax);
+            }
+        }
+        /* Eq. 5: posterior and hard decision. */
+        for (int32_t v = 0; v < n; ++v) {
+            double acc = Lch[v];
+            for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) acc += r[a->vedge[k]];
+            L[v] = acc;
+            xhat[v] = acc < 0.0;
+        }
+        used = l;
+        /* Step 5: stop on a syndrome match when early termination is on. */
+        if (J->early_term && syndrome_ok(a, xhat, s)) { conv = 1; break; }
+    }
+    if (!conv) conv = syndrome_ok(a, xhat, s);
+    if (J->post) memcpy(J->post + (size_t)b * n, L, sizeof(double) * (size_t)n);
+    memcpy(J->bits + (size_t)b * n, xhat, (size_t)n);
+    J->converged[b] = (uint8_t)conv;
+    J->iters_used[b] = used;
+    free(Lch); free(L); free(q); free(r); free(phiq); free(xhat);
+    return ORACLE_OK;
+}
+
+static void *decode_worker(void *arg) {
+    decode_job *J = arg;
+    for (;;) {
+        int b = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (b >= J->batch) break;
+        int st = decode_one(J, b);
+        if (st != ORACLE_OK) __atomic_store_n(&J->status, st, __ATOMIC_RELAXED);
+    }
+    return NULL;
+}
+
+static int run_workers(void *(*fn)(void *), void *job, int32_t n_threads, int32_t batch) {
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > batch) n_threads = batch;
+    if (n_threads <= 1) { fn(job); return ORACLE_OK; }
+    pthread_t *th = malloc(sizeof(pthread_t) * (size_t)n_threads);
+    if (!th) return ORACLE_ENOMEM;
+    int started = 0;
+    for (int i = 0; i < n_threads; ++i) {
+        if (pthread_create(&th[i], NULL, fn, job) != 0) break;
+        ++started;
+    }
+    if (started == 0) fn(job);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    free(th);
+    return ORACLE_OK;
+}
+
+int oracle_decode(int32_t n_vn, int32_t n_cn, int64_t n_edges,
+                  const int32_t *edge_vn, const int32_t *edge_cn,
+                  int32_t batch, const double *llr, const uint8_t *syndrome,
+                  int32_t max_iters, int32_t early_term, double lmax,
+                  double *post, uint8_t *bits, uint8_t *converged,
+                  int32_t *iters_used, int32_t n_threads) {
+    if (n_vn < 0 || n_cn < 0 || n_edges < 0 || batch < 0 || max_iters < 0 || !(lmax > 0.0))
+        return ORACLE_EINVAL;
+    if (batch == 0) return ORACLE_OK;
+    if (!llr || !syndrome || !bits || !converged || !iters_used) return ORACLE_EINVAL;
+    adjacency a;
+    int st = adj_build(&a, n_vn, n_cn, n_edges, edge_vn, edge_cn);
+    if (st != ORACLE_OK) return st;
+    decode_job J = {&a, llr, syndrome, batch, max_iters, early_term, lmax,
+                    post, bits, converged, iters_used, 0, ORACLE_OK};
+    st = run_workers(decode_worker, &J, n_threads, batch);
+    adj_free(&a);
+    return st != ORACLE_OK ? st : J.status;
+}
+
+/* Check H xhat = s for a batch of hard decisions (uint8 0/1 per bit). */
+int oracle_syndrome_ok(int32_t n_vn, int32_t n_cn, int64_t n_edges,
+                       const int32_t *edge_vn, const int32_t *edge_cn,
+                       int32_t batch, const uint8_t *bits, const uint8_t *syndrome,
+                       uint8_t *ok) {
+    adjacency a;
+    int st = adj_build(&a, n_vn, n_cn, n_edges, edge_vn, edge_cn);
+    if (st != ORACLE_OK) return st;
+    for (int32_t b = 0; b < batch; ++b)
+        ok[b] = (uint8_t)syndrome_ok(&a, bits + (size_t)b * n_vn, syndrome + (size_t)b * n_cn);
+    adj_free(&a);
+    return ORACLE_OK;
+}

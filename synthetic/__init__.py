@@ -1,0 +1,25 @@
+"""Seeded synthetic inputs for the MET-LDPC decoder and its oracle.
+
+This module is shared by the CUDA decoder's tests/benchmark and by the FP64
+oracle's tests.  It holds no belief-propagation arithmetic: it only builds
+the workload the decoder is given.
+
+* :mod:`synthetic.ensemble` -- a seeded multi-edge-type (MET) LDPC Tanner
+  graph of the shape used for continuous-variable QKD reconciliation
+  (core variable nodes of high degree, one degree-1 variable node per
+  type-2 check), as edge arrays.
+* :mod:`synthetic.channel` -- Bob's random string ``x``, his syndrome
+  ``s = H x`` (the sender's side of the protocol, Step 1 of the paper's
+  Methods), and Alice's binary-input AWGN observation ``y = (1-2x) + sigma*z``,
+  with ``sigma`` solved from a target reconciliation efficiency ``beta``.
+"""
+from .ensemble import MetGraph, met_ensemble, RATE_PRESETS, preset_graph
+from .channel import (biawgn_capacity, awgn_capacity, sigma_for_beta,
+                      random_bits, bob_syndrome, biawgn_observe, Workload,
+                      make_workload)
+
+__all__ = [
+    "MetGraph", "met_ensemble", "RATE_PRESETS", "preset_graph",
+    "biawgn_capacity", "awgn_capacity", "sigma_for_beta", "random_bits",
+    "bob_syndrome", "biawgn_observe", "Workload", "make_workload",
+]
