@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Decoded Mbit/s of batched syndrome-based sum-product BP on one GB300.
+
+Workload (defaults): the rate-0.1 synthetic MET-LDPC ensemble at n = 10^6,
+64 codewords per batch, 100 fixed flooding iterations, sigma from
+beta = 0.90 (BIAWGN capacity), half-precision message storage with float
+arithmetic.  One step = one mld_decode_y call over the whole batch: interleave,
+100 x (check update + variable update), final hard decision and syndrome
+check, de-interleave.  The message state (578 MB at f16) and the inputs
+(256 MB) exceed the 129 MB L2, so no flush is needed between steps.
+
+Reported: ``value`` (device-resident inputs), ``e2e`` (host pinned inputs and
+outputs through the same public call, copies inside the timed region), the
+roofline of the dominant kernel (check update) from per-launch CUDA events,
+clocks sampled during the timed region, and the FP64 oracle timed on the
+host cores (``cpu_baseline``).  ``--impl reference`` times the oracle alone.
+
+Under torchrun (N > 1) every rank decodes its own batch on its own GPU with
+no collective on the data path (replicas); the timing uses a barrier and the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "decoded Mbit/s at n=1e6, 64 codewords, fixed iters"
+UNIT = "Mbit/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rate", type=float, default=0.1)
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--msg", default="f16", choices=["f16", "f32"])
+    ap.add_argument("--slab", type=int, default=0)
+    ap.add_argument("--beta", type=float, default=0.90)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+DEFAULT_ITERS = {0.1: 100, 0.05: 150, 0.02: 200}
+
+
+def workload_config(a) -> dict:
+    return {
+        "workload": (f"synthetic MET-LDPC rate {a.rate}, n={a.n}, {a.batch} codewords, "
+                     f"{a.iters} fixed BP iterations, beta={a.beta}"),
+        "rate": a.rate, "n": a.n, "codewords": a.batch, "iters": a.iters,
+        "beta": a.beta, "msg_storage": a.msg,
+        "l2": "inputs and message state larger than L2 (no flush needed)",
+        "parallelism": "replicas",
+    }
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(wl, codewords: int, iters: int, threads: int) -> float:
+    """Wall time of the FP64 oracle on the first `codewords` of the batch."""
+    import oracle
+    t = time.perf_counter()
+    oracle.decode_y(wl.graph, wl.y[:codewords], wl.sigma[:codewords], wl.s[:codewords],
+                    iters=iters, threads=threads)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(wl, a) -> dict:
+    """Oracle throughput extrapolated to the full iteration count.
+
+    Runs the oracle on `cores` codewords for 1 and for 3 iterations; the
+    difference gives the per-iteration cost, the rest the fixed cost.
+    """
+    cores = host_cores()
+    c = max(1, min(cores, a.batch))
+    t1 = oracle_sample(wl, c, 1, c)
+    t3 = oracle_sample(wl, c, 3, c)
+    per_it = max((t3 - t1) / 2.0, 1e-9)
+    fixed = max(t1 - per_it, 0.0)
+    t_full = fixed + a.iters * per_it
+    return {"value": c * a.n / t_full / 1e6, "unit": UNIT, "cores": c, "kind": "oracle",
+            "sample": (f"{c} codewords x n={a.n}, 1 and 3 iterations timed "
+                       f"({t1:.2f} s, {t3:.2f} s), extrapolated to {a.iters} iterations")}
+
+
+def run_reference(a, wl):
+    """The oracle as it stands, timed on the host cores (rank 0 only)."""
+    cores = host_cores()
+    c = max(1, min(cores, a.batch))
+    k = 3
+    for _ in range(a.warmup):
+        oracle_sample(wl, c, k, c)
+    times = [oracle_sample(wl, c, k, c) for _ in range(a.steps)]
+    t = sum(times)
+    # each step decodes c codewords for k of the a.iters iterations
+    value = a.steps * c * a.n * k / a.iters / t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded MET ensemble, BIAWGN samples)", "config": workload_config(a),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": c, "kind": "oracle",
+                         "sample": f"each step: {c} codewords x n={a.n} x {k} iterations "
+                                   f"(value scaled to {a.iters} iterations)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = (uuid or "").lower().replace("gpu-", "")
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 10:
+                continue
+            if self.uuid and p[1].lower().replace("gpu-", "") != self.uuid:
+                continue
+            rows.append(p)
+        if not rows:
+            return None
+        try:
+            sm = [float(r[2]) for r in rows]
+            smax = max(float(r[3]) for r in rows)
+        except ValueError:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peak_hbm() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def main():
+    a = parse()
+    if a.iters is None:
+        a.iters = DEFAULT_ITERS.get(a.rate, 100)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from synthetic import make_workload
+    seed_graph = 2  # 1 + index of the n = 10^6 workload
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        wl = make_workload(a.rate, a.n, min(a.batch, host_cores()), seed_graph, 1000, beta=a.beta)
+        run_reference(a, wl)
+        return
+
+    import torch
+    import paper_1711_01783_gb300 as mld
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl = make_workload(a.rate, a.n, a.batch, seed_graph, 1000 + 64 * rank, beta=a.beta)
+    g = mld.Graph.from_edges(wl.graph)
+    dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, slab_width=a.slab)
+    st = g.stats
+    y = torch.from_numpy(wl.y).to(dev)
+    sig = torch.from_numpy(wl.sigma).to(dev)
+    syn = torch.from_numpy(wl.s).to(dev)
+    out = dict(bits=torch.empty((a.batch, a.n), dtype=torch.uint8, device=dev), post=None,
+               converged=torch.empty(a.batch, dtype=torch.uint8, device=dev),
+               iters_used=torch.empty(a.batch, dtype=torch.int32, device=dev))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dec.decode_y(y, sig, syn, a.iters, out=out)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs -----------------------------
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    dec.timing(True)
+    dec.read_timing()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    dec.timing(False)
+    kt = dec.read_timing()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    launches = torch.tensor([kt["check_launches"] + kt["var_launches"] + kt["syndrome_launches"]
+                             + kt["layout_launches"]], dtype=torch.int64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(launches, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    bits_total = world * a.batch * a.n * a.steps
+    value = bits_total / (ms_max * 1e-3) / 1e6
+
+    # ---- end to end through the host-pointer path ---------------------------
+    e2e = None
+    if not a.no_e2e:
+        y_h = torch.from_numpy(wl.y).pin_memory()
+        sig_h = torch.from_numpy(wl.sigma).pin_memory()
+        s_h = torch.from_numpy(wl.s).pin_memory()
+        out_h = dict(bits=torch.empty((a.batch, a.n), dtype=torch.uint8).pin_memory(), post=None,
+                     converged=torch.empty(a.batch, dtype=torch.uint8).pin_memory(),
+                     iters_used=torch.empty(a.batch, dtype=torch.int32).pin_memory())
+        dec.decode_y(y_h, sig_h, s_h, a.iters, out=out_h)  # warm the path
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(a.e2e_steps):
+            dec.decode_y(y_h, sig_h, s_h, a.iters, out=out_h)  # waits for the stream
+        h1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        te = torch.tensor([max(h0.elapsed_time(h1), wall * 1e3)], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        h2d = a.batch * a.n * 4 + a.batch * 4 + a.batch * st["n_cn"]
+        d2h = a.batch * a.n + a.batch + 4 * a.batch
+        e2e = {"value": world * a.batch * a.n * a.e2e_steps / (float(te.item()) * 1e-3) / 1e6,
+               "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- roofline of the check update ---------------------------------------
+    b = 2 if a.msg == "f16" else 4
+    per_cw = 2 * b * st["e_core"] + 4 * st["n_core"] + 4 * st["n_deg1"] + st["n_cn"] / 8
+    check_ms = kt["check_ms"] / max(1, kt["check_launches"])
+    achieved = per_cw * a.batch / (check_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_check_update", "peak_kind": peak_kind,
+                "launch_ms": check_ms, "algorithmic_bytes_per_launch": per_cw * a.batch,
+                "var_update_ms": kt["var_ms"] / max(1, kt["var_launches"]),
+                "share_check": kt["check_ms"] / max(1e-9, kt["check_ms"] + kt["var_ms"] + kt["syndrome_ms"]
+                                                    + kt["layout_ms"])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(wl, a)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded MET ensemble, BIAWGN samples)", "config": workload_config(a),
+            "e2e": e2e, "gpu_launches": int(launches.item()), "roofline": roofline,
+            "cpu_baseline": cpu, "clocks": clk,
+            "frames_converged": int(out["converged"].sum().item()),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

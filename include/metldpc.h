@@ -1,0 +1,202 @@
+/*
+ * metldpc.h -- C ABI of the batched MET-LDPC belief-propagation decoder
+ * (libmetldpc.so, CUDA for sm_103a).
+ *
+ * The decoder performs the error-correction step of reverse reconciliation
+ * in continuous-variable QKD as described in arXiv:1711.01783: Bob sends
+ * the syndrome s = H x of his bits (Methods, Step 1); Alice decodes her soft
+ * observation of x with flooding sum-product belief propagation (Methods,
+ * Steps 2-5, Eqs. 1-5), many codewords at once (Results, "High speed error
+ * correction with MET-LDPC codes").
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: MLD_OK (0) or a negative MLD_E* status.  The text of the
+ *    last error raised on the calling thread is returned by mld_last_error().
+ *  - Ownership: buffers passed in are owned by the caller and never freed by
+ *    the library.  Opaque handles are freed by their *_destroy function.
+ *  - Streams: every call that touches the device takes a cudaStream_t passed
+ *    as `void *stream` (NULL = the legacy default stream).  Work is enqueued
+ *    on that stream; the library never synchronizes the device.  With host
+ *    buffers (no MLD_DEVICE_PTRS) the results are valid once that stream has
+ *    been synchronized.
+ *  - Device: handles are bound to the CUDA device that was current when they
+ *    were created; calls must be made with that device current.
+ *  - LLRs follow L = ln p(x=0)/p(x=1); a bit is decided 1 iff its posterior
+ *    is negative (a posterior of exactly 0 decides 0).  This is the LLR form
+ *    of the ratio q(1)/q(0) and of the decision "c_i = 1 iff q_i > 1" in
+ *    Methods, Step 5.
+ *  - Bits, syndromes and flags are one uint8_t (0 or 1) per value; arrays
+ *    indexed [codeword][node] are row-major with the node index fastest, in
+ *    the caller's node numbering.
+ */
+#ifndef METLDPC_H
+#define METLDPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define MLD_OK        0
+#define MLD_EINVAL   (-1)  /* bad argument (null pointer, size, flag, dtype)   */
+#define MLD_ENOMEM   (-2)  /* host or device allocation failed                  */
+#define MLD_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed        */
+#define MLD_ETIMEOUT (-4)  /* a bounded device-side wait gave up                 */
+#define MLD_EGRAPH   (-5)  /* malformed Tanner graph (index out of range, ...)   */
+
+/* ---- edge-message storage type (mld_opts.msg_dtype) ---------------------- */
+#define MLD_MSG_F32 0      /* check-to-variable messages stored as float       */
+#define MLD_MSG_F16 1      /* stored as IEEE half (round to nearest even);
+                              all arithmetic stays in float                    */
+
+/* ---- decode flags -------------------------------------------------------- */
+#define MLD_EARLY_TERM  0x1u  /* stop each codeword at the first iteration l >= 1
+                                 whose hard decision satisfies H x = s
+                                 (Methods, Step 5)                             */
+#define MLD_DEVICE_PTRS 0x2u  /* all data pointers of the call are device
+                                 memory; otherwise they are host memory and the
+                                 library stages them through its own buffers  */
+
+typedef struct mld_graph mld_graph;
+typedef struct mld_decoder mld_decoder;
+
+/* Text of the last error raised on the calling thread ("" if none).  The
+ * pointer stays valid until the next library call on this thread. */
+const char *mld_last_error(void);
+
+/* Library version string, e.g. "metldpc 0.1.0 sm_103a". */
+const char *mld_version(void);
+
+/* ---- Tanner graph --------------------------------------------------------
+ * mld_graph_create: build the decoder's graph store from an edge list and
+ * upload it to the current device.  H has n_cn rows (checks) and n_vn columns
+ * (variable nodes, VNs); edge k joins VN edge_vn[k] and check edge_cn[k]
+ * (Methods: R_j = VNs of check j, C_i = checks of VN i).
+ *   edge_vn, edge_cn : host int32 [n_edges], 0 <= edge_vn < n_vn,
+ *                      0 <= edge_cn < n_cn; each (VN, check) pair at most once.
+ *   edge_type        : host uint8 [n_edges] in [0, MLD_MAX_EDGE_TYPES) or NULL
+ *                      (all 0); it selects the weight of weighted BP only.
+ * VNs of degree 1 carry no stored message: their variable-to-check message
+ * is always their channel LLR, so they are left out of the iterations and
+ * their posteriors are formed from the last check update (the "ignored VNs"
+ * of Table 1 and the Discussion).  Errors: MLD_EINVAL for null/negative
+ * arguments, MLD_EGRAPH for an out-of-range index, a repeated pair or more
+ * than 2^31-1 edges, MLD_ENOMEM, MLD_ECUDA.  *out is set only on success. */
+#define MLD_MAX_EDGE_TYPES 8
+int mld_graph_create(const int32_t *edge_vn, const int32_t *edge_cn,
+                     const uint8_t *edge_type, int64_t n_edges,
+                     int32_t n_vn, int32_t n_cn, mld_graph **out);
+int mld_graph_destroy(mld_graph *g);
+
+typedef struct {
+    int32_t n_vn, n_cn;
+    int64_t n_edges;
+    int32_t n_core;        /* VNs of degree != 1 (updated every iteration)   */
+    int32_t n_deg1;        /* VNs of degree 1 (skipped during iterations)     */
+    int64_t e_core;        /* edges between checks and core VNs = stored
+                              messages = n_edges - n_deg1 (Table 1, "edges
+                              to pass messages")                             */
+    int32_t max_check_deg; /* max check degree (core + degree-1 edges)       */
+    int32_t max_vn_deg;
+} mld_graph_stats;
+int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out);
+
+/* ---- decoder --------------------------------------------------------------
+ * mld_decoder_create: allocate the device state for decoding up to
+ * opts->max_batch codewords of graph g at once.  The graph must outlive the
+ * decoder.  Codewords are interleaved in slabs of `slab_width` (the paper's
+ * "raw key permutation", Results): the message of one edge for one slab is a
+ * contiguous run of slab_width values, so every graph gather is a full cache
+ * line.  opts fields:
+ *   msg_dtype  : MLD_MSG_F32 or MLD_MSG_F16.
+ *   max_batch  : >= 1.
+ *   lmax       : LLR clamp (> 0; 0 selects 25).  Channel LLRs, messages and
+ *                the arguments of phi are kept within it (see mld_decode).
+ *   slab_width : 8, 16, 32 or 64 codewords per slab; 0 selects 32 for F32
+ *                and 64 for F16.
+ * Errors: MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA. */
+typedef struct {
+    int32_t msg_dtype;
+    int32_t max_batch;
+    float lmax;
+    int32_t slab_width;
+    int32_t reserved[12];  /* must be zero */
+} mld_opts;
+int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out);
+int mld_decoder_destroy(mld_decoder *d);
+
+/* mld_decode: sum-product BP on `batch` codewords (Methods, Steps 2-5).
+ *   llr        : float [batch][n_vn], channel LLRs 2y/sigma^2 (Eq. 1 in LLR
+ *                form), clamped to [-lmax, lmax] on entry.
+ *   syndrome   : uint8 [batch][n_cn], Bob's syndrome s = H x (Step 1).
+ *   batch      : 0 <= batch <= max_batch (0 does nothing).
+ *   max_iters  : >= 0 flooding iterations; one iteration = check update
+ *                (Eqs. 2-3, with the factor (1 - 2 s_j) of check j) then
+ *                variable update (Eq. 4).  Per iteration, for check c and
+ *                core edge e = (v, c):
+ *                  q_e = clamp(L_v - r_e, lmax)   (degree-1 VN: q = L_ch(v))
+ *                  r_e = (1-2s_c) prod_{e' != e} sgn q_e'
+ *                        * phi(clamp(sum_{e' != e} phi(clamp(|q_e'|))))
+ *                  L_v = L_ch(v) + sum_{e in C_v} r_e        (Eqs. 4-5)
+ *                with phi(x) = -ln tanh(x/2) evaluated in float and its
+ *                arguments kept in [phi(lmax), lmax].
+ *   flags      : MLD_EARLY_TERM, MLD_DEVICE_PTRS.
+ *   bits_out   : uint8 [batch][n_vn], hard decisions x = [L < 0] (Step 5).
+ *   post_out   : float [batch][n_vn] posteriors L (Eq. 5), or NULL.
+ *   converged  : uint8 [batch], 1 iff H bits = s.  Without MLD_EARLY_TERM
+ *                exactly max_iters iterations run and this is still set.
+ *   iters_used : int32 [batch]; max_iters without MLD_EARLY_TERM; with it,
+ *                the first l >= 1 with H x^l = s (outputs are x^l, L^l), else
+ *                max_iters.
+ * Errors: MLD_EINVAL (null pointer, batch > max_batch, negative max_iters,
+ * unknown flag), MLD_ECUDA.  A device-detected error, if any, is reported
+ * by mld_decode_status once the stream has completed. */
+int mld_decode(mld_decoder *d, const float *llr, const uint8_t *syndrome,
+               int32_t batch, int32_t max_iters, uint32_t flags,
+               uint8_t *bits_out, float *post_out, uint8_t *converged,
+               int32_t *iters_used, void *stream);
+
+/* mld_decode_y: as mld_decode, from Alice's BIAWGN observation
+ * y = (1 - 2x) + sigma z instead of LLRs; the channel LLR 2 y / sigma_b^2
+ * (Eq. 1 in LLR form) is formed on the device.
+ *   y     : float [batch][n_vn];  sigma : float [batch], each > 0 (host or
+ *   device memory like the other pointers).  A sigma <= 0 yields LLR 0 for
+ *   that codeword's bits (no information) rather than an error. */
+int mld_decode_y(mld_decoder *d, const float *y, const float *sigma,
+                 const uint8_t *syndrome, int32_t batch, int32_t max_iters,
+                 uint32_t flags, uint8_t *bits_out, float *post_out,
+                 uint8_t *converged, int32_t *iters_used, void *stream);
+
+/* Status of device-detected errors for work already completed on the stream
+ * (MLD_OK if none).  Synchronizes nothing; call after the stream is idle. */
+int mld_decode_status(mld_decoder *d);
+
+/* ---- kernel timing (measurement hook) -------------------------------------
+ * With timing enabled, every later decode call on d records a pair of CUDA
+ * events on its stream around each kernel it launches.  mld_decoder_timing_read
+ * waits for those events, returns the device time and launch count summed per
+ * kernel class since the last read, and clears them.  Classes: check update
+ * (Eqs. 2-3), variable update (Eqs. 4-5), syndrome check (Step 5) and
+ * layout kernels (interleave / de-interleave / bit packing).  Enabling adds
+ * two event records per launch and changes no result.  Errors: MLD_EINVAL,
+ * MLD_ECUDA. */
+typedef struct {
+    double check_ms, var_ms, syndrome_ms, layout_ms;
+    int64_t check_launches, var_launches, syndrome_launches, layout_launches;
+} mld_timing;
+int mld_decoder_timing_enable(mld_decoder *d, int enable);
+int mld_decoder_timing_read(mld_decoder *d, mld_timing *out);
+
+/* ---- phi evaluation (verification hook) ----------------------------------
+ * Evaluates on the device the float phi(x) = -ln tanh(x/2) that the check
+ * update uses (the LLR-domain message map that the closing paragraph of the
+ * Methods proposes to tabulate), for n inputs clamped to [phi(lmax), lmax]
+ * with lmax = 25.  x and out are device float pointers [n]. */
+int mld_phi_eval(const float *x, float *out, int64_t n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* METLDPC_H */

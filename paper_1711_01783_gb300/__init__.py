@@ -1,0 +1,288 @@
+"""Batched MET-LDPC belief-propagation decoder for GB300 (sm_103a).
+
+Thin ctypes binding over ``libmetldpc.so`` (C ABI in ``include/metldpc.h``):
+argument marshalling only; every decoding step runs in the library's CUDA
+kernels.  Device tensors (torch, CUDA) are passed as device pointers on the
+current torch stream; numpy arrays or CPU tensors go through the library's
+host-staging path and the call waits for the stream before returning.
+
+The library must have been built (``python -m paper_1711_01783_gb300.build``
+or ``__graft_entry__.build()``); the first call into the package raises
+ImportError if it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmetldpc.so")
+
+MLD_OK = 0
+MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA, MLD_ETIMEOUT, MLD_EGRAPH = -1, -2, -3, -4, -5
+MLD_MSG_F32, MLD_MSG_F16 = 0, 1
+MLD_EARLY_TERM, MLD_DEVICE_PTRS = 0x1, 0x2
+
+_STATUS = {MLD_EINVAL: "MLD_EINVAL", MLD_ENOMEM: "MLD_ENOMEM", MLD_ECUDA: "MLD_ECUDA",
+           MLD_ETIMEOUT: "MLD_ETIMEOUT", MLD_EGRAPH: "MLD_EGRAPH"}
+
+# Every symbol include/metldpc.h declares.
+EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destroy",
+           "mld_graph_stats_get", "mld_decoder_create", "mld_decoder_destroy", "mld_decode",
+           "mld_decode_y", "mld_decode_status", "mld_decoder_timing_enable",
+           "mld_decoder_timing_read", "mld_phi_eval")
+
+
+class MldError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GraphStats(ctypes.Structure):
+    _fields_ = [("n_vn", ctypes.c_int32), ("n_cn", ctypes.c_int32), ("n_edges", ctypes.c_int64),
+                ("n_core", ctypes.c_int32), ("n_deg1", ctypes.c_int32), ("e_core", ctypes.c_int64),
+                ("max_check_deg", ctypes.c_int32), ("max_vn_deg", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("msg_dtype", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("lmax", ctypes.c_float), ("slab_width", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 12)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("check_ms", ctypes.c_double), ("var_ms", ctypes.c_double),
+                ("syndrome_ms", ctypes.c_double), ("layout_ms", ctypes.c_double),
+                ("check_launches", ctypes.c_int64), ("var_launches", ctypes.c_int64),
+                ("syndrome_launches", ctypes.c_int64), ("layout_launches", ctypes.c_int64)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_1711_01783_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U32, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float
+    sig = {
+        "mld_last_error": (ctypes.c_char_p, []),
+        "mld_version": (ctypes.c_char_p, []),
+        "mld_graph_create": (ctypes.c_int, [P, P, P, I64, I32, I32, ctypes.POINTER(P)]),
+        "mld_graph_destroy": (ctypes.c_int, [P]),
+        "mld_graph_stats_get": (ctypes.c_int, [P, ctypes.POINTER(GraphStats)]),
+        "mld_decoder_create": (ctypes.c_int, [P, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
+        "mld_decoder_destroy": (ctypes.c_int, [P]),
+        "mld_decode": (ctypes.c_int, [P, P, P, I32, I32, U32, P, P, P, P, P]),
+        "mld_decode_y": (ctypes.c_int, [P, P, P, P, I32, I32, U32, P, P, P, P, P]),
+        "mld_decode_status": (ctypes.c_int, [P]),
+        "mld_decoder_timing_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "mld_decoder_timing_read": (ctypes.c_int, [P, ctypes.POINTER(Timing)]),
+        "mld_phi_eval": (ctypes.c_int, [P, P, I64, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises ImportError if it has not been built."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def version() -> str:
+    return lib().mld_version().decode()
+
+
+def _check(status: int):
+    if status != MLD_OK:
+        raise MldError(status, lib().mld_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_cuda_tensor(x) -> bool:
+    return getattr(x, "is_cuda", False)
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+class Graph:
+    """Tanner graph uploaded to the current CUDA device (mld_graph_create)."""
+
+    def __init__(self, edge_vn, edge_cn, n_vn: int, n_cn: int, edge_type=None):
+        ev = np.ascontiguousarray(edge_vn, dtype=np.int32)
+        ec = np.ascontiguousarray(edge_cn, dtype=np.int32)
+        et = None if edge_type is None else np.ascontiguousarray(edge_type, dtype=np.uint8)
+        if ev.shape != ec.shape or (et is not None and et.shape != ev.shape):
+            raise ValueError("edge arrays differ in length")
+        h = ctypes.c_void_p()
+        _check(lib().mld_graph_create(_ptr(ev), _ptr(ec), _ptr(et), ev.shape[0], int(n_vn), int(n_cn),
+                                     ctypes.byref(h)))
+        self._h = h
+        st = GraphStats()
+        _check(lib().mld_graph_stats_get(h, ctypes.byref(st)))
+        self.stats = {f: getattr(st, f) for f, _ in GraphStats._fields_}
+        self.n_vn, self.n_cn = int(n_vn), int(n_cn)
+
+    @classmethod
+    def from_edges(cls, g):
+        """From any object with n_vn, n_cn, edge_vn, edge_cn (and edge_type)."""
+        return cls(g.edge_vn, g.edge_cn, g.n_vn, g.n_cn, getattr(g, "edge_type", None))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mld_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Decoder:
+    """Device state for decoding up to ``max_batch`` codewords (mld_decoder_create)."""
+
+    def __init__(self, graph: Graph, max_batch: int, msg_dtype: str = "f32",
+                 lmax: float = 25.0, slab_width: int = 0):
+        o = Opts()
+        o.msg_dtype = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
+        o.max_batch = int(max_batch)
+        o.lmax = float(lmax)
+        o.slab_width = int(slab_width)
+        h = ctypes.c_void_p()
+        _check(lib().mld_decoder_create(graph.handle, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.graph = graph  # keeps the graph alive
+        self.max_batch = int(max_batch)
+        self.msg_dtype = msg_dtype
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mld_decoder_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _outputs(self, B: int, on_device: bool, want_post: bool, out):
+        n = self.graph.n_vn
+        if out is not None:
+            return out
+        if on_device:
+            torch = _torch()
+            dev = torch.device("cuda", torch.cuda.current_device())
+            return dict(bits=torch.empty((B, n), dtype=torch.uint8, device=dev),
+                        post=torch.empty((B, n), dtype=torch.float32, device=dev) if want_post else None,
+                        converged=torch.empty(B, dtype=torch.uint8, device=dev),
+                        iters_used=torch.empty(B, dtype=torch.int32, device=dev))
+        return dict(bits=np.empty((B, n), dtype=np.uint8),
+                    post=np.empty((B, n), dtype=np.float32) if want_post else None,
+                    converged=np.empty(B, dtype=np.uint8),
+                    iters_used=np.empty(B, dtype=np.int32))
+
+    def _run(self, fn, x, sigma, syndrome, iters, early_term, want_post, out, stream):
+        on_dev = _is_cuda_tensor(x)
+        if on_dev:
+            torch = _torch()
+            x = x.contiguous()
+            if x.dtype != torch.float32:
+                raise TypeError("soft input must be float32")
+            syndrome = syndrome.contiguous().to(torch.uint8)
+            if sigma is not None:
+                sigma = sigma.contiguous().to(torch.float32)
+        else:
+            x = np.ascontiguousarray(x.numpy() if hasattr(x, "numpy") else x, dtype=np.float32)
+            syndrome = np.ascontiguousarray(syndrome.numpy() if hasattr(syndrome, "numpy") else syndrome,
+                                            dtype=np.uint8)
+            if sigma is not None:
+                sigma = np.ascontiguousarray(sigma.numpy() if hasattr(sigma, "numpy") else sigma,
+                                             dtype=np.float32).reshape(-1)
+        B = int(x.shape[0])
+        if tuple(x.shape) != (B, self.graph.n_vn) or tuple(syndrome.shape) != (B, self.graph.n_cn):
+            raise ValueError("soft input must be [B, n_vn] and syndrome [B, n_cn]")
+        o = self._outputs(B, on_dev, want_post, out)
+        flags = (MLD_EARLY_TERM if early_term else 0) | (MLD_DEVICE_PTRS if on_dev else 0)
+        sh = _stream_handle(stream)
+        args = [self._h, _ptr(x)]
+        if fn is lib().mld_decode_y:
+            args.append(_ptr(sigma))
+        args += [_ptr(syndrome), B, int(iters), flags, _ptr(o["bits"]), _ptr(o.get("post")),
+                 _ptr(o["converged"]), _ptr(o["iters_used"]), sh]
+        _check(fn(*args))
+        if not on_dev:
+            torch = _torch()
+            (stream or torch.cuda.current_stream()).synchronize()
+        return o
+
+    def decode(self, llr, syndrome, iters: int, early_term: bool = False,
+               want_post: bool = False, out=None, stream=None):
+        """Decode from channel LLRs [B, n]; see mld_decode."""
+        return self._run(lib().mld_decode, llr, None, syndrome, iters, early_term, want_post, out, stream)
+
+    def decode_y(self, y, sigma, syndrome, iters: int, early_term: bool = False,
+                 want_post: bool = False, out=None, stream=None):
+        """Decode from BIAWGN observations y [B, n] and per-codeword sigma [B]."""
+        return self._run(lib().mld_decode_y, y, sigma, syndrome, iters, early_term, want_post, out, stream)
+
+    def status(self) -> int:
+        return int(lib().mld_decode_status(self._h))
+
+    def timing(self, enable: bool):
+        """Record CUDA events around each kernel of later decode calls."""
+        _check(lib().mld_decoder_timing_enable(self._h, int(bool(enable))))
+
+    def read_timing(self) -> dict:
+        """Per-kernel-class device time (ms) and launch counts since the last read."""
+        t = Timing()
+        _check(lib().mld_decoder_timing_read(self._h, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in Timing._fields_}
+
+
+def phi(x, stream=None):
+    """Device phi(x) = -ln tanh(x/2) as used by the check update (float32 CUDA tensor)."""
+    torch = _torch()
+    x = x.contiguous().to(torch.float32)
+    out = torch.empty_like(x)
+    _check(lib().mld_phi_eval(_ptr(x), _ptr(out), x.numel(), _stream_handle(stream)))
+    return out
+
+
+__all__ = ["Graph", "Decoder", "phi", "version", "lib", "MldError", "EXPORTS", "LIB_PATH"]

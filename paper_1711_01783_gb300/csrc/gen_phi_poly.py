@@ -1,0 +1,65 @@
+"""Generate phi_poly.h: polynomial pieces of the float phi(x) = -ln tanh(x/2).
+
+Build-time script for the CUDA decoder (run by hand when the split point or
+degrees change; its output is committed).  The device evaluates phi on
+[phi(25), 25] as
+
+  x <  X0 :  phi(x) = ln 2 - ln(x) - t * Ps(t),      t = x^2
+             where t * Ps(t) approximates h(x) = ln(tanh(x/2) / (x/2)),
+             an even function analytic for |x| < pi;
+  x >= X0 :  phi(x) = 2 atanh(e) = 2 e * Pl(e^2),    e = exp(-x)
+             where Pl(z) approximates atanh(sqrt z) / sqrt z.
+
+ln(x) and exp(-x) come from the hardware base-2 approximations (MUFU lg2 /
+ex2).  The coefficients are least-squares fits on Chebyshev nodes of the
+interval (a near-minimax fit), computed in float64 from the closed forms
+above with numpy.
+"""
+import os
+
+import numpy as np
+
+X0 = 1.25
+DEG_SMALL = 5   # coefficients of Ps
+DEG_LARGE = 4   # coefficients of Pl
+
+
+def _cheb(lo, hi, k=6000):
+    return lo + (hi - lo) * (np.cos(np.linspace(0, np.pi, k)) + 1) / 2
+
+
+def fit():
+    t = _cheb(1e-10, X0 * X0)
+    x = np.sqrt(t)
+    h = np.log(np.tanh(x / 2) / (x / 2))
+    cs = np.polynomial.polynomial.polyfit(t, h / t, DEG_SMALL - 1)
+    err_s = np.max(np.abs(np.polynomial.polynomial.polyval(t, cs) * t - h))
+    z = _cheb(1e-14, np.exp(-2 * X0))
+    e = np.sqrt(z)
+    pl = np.arctanh(e) / e
+    cl = np.polynomial.polynomial.polyfit(z, pl, DEG_LARGE - 1)
+    err_l = np.max(np.abs(np.polynomial.polynomial.polyval(z, cl) / pl - 1))
+    return cs, cl, err_s, err_l
+
+
+def main():
+    cs, cl, err_s, err_l = fit()
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "phi_poly.h")
+    lines = [
+        "// Generated by gen_phi_poly.py -- polynomial pieces of phi(x) = -ln tanh(x/2).",
+        f"// small branch x < {X0}: phi = ln2 - ln x - t*Ps(t), t = x^2; max |fit error| {err_s:.2e}",
+        f"// large branch: phi = 2e*Pl(e^2), e = exp(-x); max relative fit error {err_l:.2e}",
+        "#pragma once",
+        f"#define MLD_PHI_X0 {X0:.9g}f",
+    ]
+    for i, c in enumerate(cs):
+        lines.append(f"#define MLD_PHI_S{i} ({c:.9e}f)")
+    for i, c in enumerate(cl):
+        lines.append(f"#define MLD_PHI_L{i} ({c:.9e}f)")
+    with open(out, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    print(out, err_s, err_l)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,116 @@
+// Host-side construction of the decoder's graph store from an edge list.
+//
+// The paper keeps H as "one file of VNs in order plus one file of the
+// VN-to-check mapping, roles swappable" (Results, "High speed error
+// correction with MET-LDPC codes").  Here the same information is a
+// check-major edge list (the message order) plus a VN-major permutation of
+// it, with degree-1 VNs split off because their outgoing message never
+// changes (Table 1, "Ignored VNs"; Discussion).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace mld {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+const char *last_error_text() { return g_last_error.c_str(); }
+
+int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
+                     const uint8_t *edge_type, int64_t n_edges, int32_t n_vn,
+                     int32_t n_cn, HostGraph *out) {
+    if (n_vn < 0 || n_cn < 0 || n_edges < 0)
+        return fail(MLD_EINVAL, "graph: negative size");
+    if (n_edges > 0 && (!edge_vn || !edge_cn))
+        return fail(MLD_EINVAL, "graph: null edge array");
+    if (n_edges > INT32_MAX)
+        return fail(MLD_EGRAPH, "graph: more than 2^31-1 edges");
+    HostGraph &g = *out;
+    g = HostGraph();
+    g.n_vn = n_vn;
+    g.n_cn = n_cn;
+    g.n_edges = n_edges;
+
+    std::vector<int32_t> vdeg(n_vn, 0), cdeg(n_cn, 0);
+    for (int64_t k = 0; k < n_edges; ++k) {
+        const int32_t v = edge_vn[k], c = edge_cn[k];
+        if (v < 0 || v >= n_vn || c < 0 || c >= n_cn)
+            return fail(MLD_EGRAPH, "graph: edge " + std::to_string(k) + " has an index out of range");
+        if (edge_type && edge_type[k] >= MLD_MAX_EDGE_TYPES)
+            return fail(MLD_EGRAPH, "graph: edge type out of range at edge " + std::to_string(k));
+        vdeg[v]++;
+        cdeg[c]++;
+    }
+    // check-major order of all edges, ties broken by VN -> detects repeats
+    std::vector<int32_t> order(n_edges);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (edge_cn[a] != edge_cn[b]) return edge_cn[a] < edge_cn[b];
+        return edge_vn[a] < edge_vn[b];
+    });
+    for (int64_t i = 1; i < n_edges; ++i)
+        if (edge_cn[order[i]] == edge_cn[order[i - 1]] && edge_vn[order[i]] == edge_vn[order[i - 1]])
+            return fail(MLD_EGRAPH, "graph: repeated (VN, check) pair at edge " + std::to_string(order[i]));
+
+    // internal VN numbering
+    std::vector<int32_t> core_id(n_vn, -1);
+    for (int32_t v = 0; v < n_vn; ++v)
+        if (vdeg[v] != 1) core_id[v] = g.n_core++;
+    g.n_deg1 = n_vn - g.n_core;
+    g.e_core = static_cast<int32_t>(n_edges - g.n_deg1);
+    g.unit.assign(n_vn, -1);
+    for (int32_t v = 0; v < n_vn; ++v)
+        if (core_id[v] >= 0) g.unit[v] = core_id[v];
+
+    g.cptr.assign(static_cast<size_t>(n_cn) + 1, 0);
+    g.dptr.assign(static_cast<size_t>(n_cn) + 1, 0);
+    g.col.resize(g.e_core);
+    g.etype_core.resize(g.e_core);
+    g.etype_deg1.resize(g.n_deg1);
+    int32_t ce = 0, slot = 0;
+    int64_t i = 0;
+    for (int32_t c = 0; c < n_cn; ++c) {
+        g.cptr[c] = ce;
+        g.dptr[c] = slot;
+        for (; i < n_edges && edge_cn[order[i]] == c; ++i) {
+            const int32_t k = order[i];
+            const int32_t v = edge_vn[k];
+            const uint8_t t = edge_type ? edge_type[k] : 0;
+            if (core_id[v] >= 0) {
+                g.col[ce] = core_id[v];
+                g.etype_core[ce] = t;
+                ++ce;
+            } else {
+                g.unit[v] = g.n_core + slot;
+                g.etype_deg1[slot] = t;
+                ++slot;
+            }
+        }
+        g.max_check_deg = std::max(g.max_check_deg, cdeg[c]);
+    }
+    g.cptr[n_cn] = ce;
+    g.dptr[n_cn] = slot;
+    // (core edges of a check are already ascending in core id because the
+    // natural order is ascending and core ids preserve it)
+
+    // VN-major view of the core edges
+    g.vptr.assign(static_cast<size_t>(g.n_core) + 1, 0);
+    for (int32_t e = 0; e < g.e_core; ++e) g.vptr[g.col[e] + 1]++;
+    for (int32_t v = 0; v < g.n_core; ++v) g.vptr[v + 1] += g.vptr[v];
+    g.vedge.resize(g.e_core);
+    std::vector<int32_t> fill(g.vptr.begin(), g.vptr.end() - 1);
+    for (int32_t e = 0; e < g.e_core; ++e) g.vedge[fill[g.col[e]]++] = e;
+    for (int32_t v = 0; v < n_vn; ++v) g.max_vn_deg = std::max(g.max_vn_deg, vdeg[v]);
+    return MLD_OK;
+}
+
+}  // namespace mld

@@ -1,0 +1,54 @@
+// Internal declarations shared by the host graph store (graph.cpp) and the
+// CUDA decoder (decoder.cu).  Not part of the public ABI (include/metldpc.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "metldpc.h"
+
+namespace mld {
+
+// Record an error for mld_last_error() and return `code`.
+int fail(int code, const std::string &msg);
+// Clear the thread's error text.
+void clear_error();
+
+// Graph store in the decoder's internal numbering (built on the host, then
+// copied to the device).
+//
+//  * Core VNs (degree != 1) are numbered 0..n_core-1 in natural order.
+//  * Degree-1 VNs get "slots" 0..n_deg1-1 in the order of their check, so that
+//    the slots of check c are the contiguous range dptr[c]..dptr[c+1].
+//  * Core edges are numbered check-major: the core edges of check c are
+//    cptr[c]..cptr[c+1] (sorted by core VN), col[e] is the core VN of edge e.
+//    This is also the order of the stored check-to-variable messages.
+//  * vptr/vedge is the VN-major view (CSC): the core edges of core VN v are
+//    vedge[vptr[v]..vptr[v+1]], ascending.
+//  * unit[j] maps natural VN j to its internal index: core VN index, or
+//    n_core + slot for a degree-1 VN.
+struct HostGraph {
+    int32_t n_vn = 0, n_cn = 0;
+    int64_t n_edges = 0;
+    int32_t n_core = 0, n_deg1 = 0;
+    int32_t e_core = 0;
+    int32_t max_check_deg = 0, max_vn_deg = 0;
+    std::vector<int32_t> cptr, col, dptr, vptr, vedge, unit;
+    std::vector<uint8_t> etype_core, etype_deg1;
+};
+
+int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
+                     const uint8_t *edge_type, int64_t n_edges, int32_t n_vn,
+                     int32_t n_cn, HostGraph *out);
+
+}  // namespace mld
+
+struct mld_graph {
+    mld::HostGraph h;
+    int device = 0;
+    // device copies of the index arrays
+    int32_t *cptr = nullptr, *col = nullptr, *dptr = nullptr;
+    int32_t *vptr = nullptr, *vedge = nullptr, *unit = nullptr;
+    uint8_t *etype_core = nullptr, *etype_deg1 = nullptr;
+};
