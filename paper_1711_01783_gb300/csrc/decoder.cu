@@ -40,7 +40,6 @@ const char *last_error_text();
 namespace {
 
 constexpr int kK = 4;          // codewords per thread
-constexpr int kMaxD = 8;       // check degree kept in registers
 constexpr int kBlock = 256;
 
 // ---------------------------------------------------------------------------
@@ -60,22 +59,52 @@ __device__ __forceinline__ float mufu_ex2(float x) {
     return y;
 }
 
-__device__ __forceinline__ float phi_f(float x) {
+__device__ __forceinline__ float phi_small(float x) {
     const float kLn2 = 0.693147180559945309f;
-    const float kLog2e = 1.442695040888963407f;
     const float t = x * x;
     float ps = fmaf(MLD_PHI_S4, t, MLD_PHI_S3);
     ps = fmaf(ps, t, MLD_PHI_S2);
     ps = fmaf(ps, t, MLD_PHI_S1);
     ps = fmaf(ps, t, MLD_PHI_S0);
-    const float small = fmaf(-t, ps, fmaf(-kLn2, mufu_lg2(x), kLn2));
+    return fmaf(-t, ps, fmaf(-kLn2, mufu_lg2(x), kLn2));
+}
+
+__device__ __forceinline__ float phi_large(float x) {
+    const float kLog2e = 1.442695040888963407f;
     const float e = mufu_ex2(-kLog2e * x);
     const float z = e * e;
     float pl = fmaf(MLD_PHI_L3, z, MLD_PHI_L2);
     pl = fmaf(pl, z, MLD_PHI_L1);
     pl = fmaf(pl, z, MLD_PHI_L0);
-    const float large = (e + e) * pl;
-    return x < MLD_PHI_X0 ? small : large;
+    return (e + e) * pl;
+}
+
+// Branch-free choice x < th ? a : b (both operands are already computed).
+__device__ __forceinline__ float sel_lt(float x, float th, float a, float b) {
+    float r;
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %1, %2;\n\tselp.f32 %0, %3, %4, p;\n\t}"
+        : "=f"(r) : "f"(x), "f"(th), "f"(a), "f"(b));
+    return r;
+}
+
+// phi of one value: both pieces, then the one for x.
+__device__ __forceinline__ float phi_f(float x) {
+    return sel_lt(x, MLD_PHI_X0, phi_small(x), phi_large(x));
+}
+
+// phi of four values.  A piece is evaluated only if some lane of the warp
+// needs it (one MUFU op per value instead of two when the warp agrees); the
+// result equals phi_f element by element.  Must be called by all 32 lanes.
+__device__ __forceinline__ float4 phi4(float4 x) {
+    const bool any_s = (x.x < MLD_PHI_X0) | (x.y < MLD_PHI_X0) | (x.z < MLD_PHI_X0) | (x.w < MLD_PHI_X0);
+    const bool any_l = !((x.x < MLD_PHI_X0) & (x.y < MLD_PHI_X0) & (x.z < MLD_PHI_X0) & (x.w < MLD_PHI_X0));
+    float4 sm = make_float4(0.f, 0.f, 0.f, 0.f), lg = sm;
+    if (__any_sync(0xFFFFFFFFu, any_s))
+        sm = make_float4(phi_small(x.x), phi_small(x.y), phi_small(x.z), phi_small(x.w));
+    if (__any_sync(0xFFFFFFFFu, any_l))
+        lg = make_float4(phi_large(x.x), phi_large(x.y), phi_large(x.z), phi_large(x.w));
+    return make_float4(sel_lt(x.x, MLD_PHI_X0, sm.x, lg.x), sel_lt(x.y, MLD_PHI_X0, sm.y, lg.y),
+                       sel_lt(x.z, MLD_PHI_X0, sm.z, lg.z), sel_lt(x.w, MLD_PHI_X0, sm.w, lg.w));
 }
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
@@ -160,14 +189,14 @@ struct CnArgs {
 
 template <typename MsgT, int W>
 __device__ __forceinline__ void emit_deg1(const CnArgs &a, int slab, int slot, int lane0,
-                                          float4 rv, uint32_t donenib) {
+                                          float4 rv, uint32_t donenib, bool valid) {
     constexpr int NB = W / 8;
     const size_t base = (static_cast<size_t>(slab) * a.n_deg1 + slot) * W + lane0;
-    const float4 l = ldf4(a.lch1 + base);
+    const float4 l = ldf4(a.lch1 + base);  // in range: the slot of a real check
     float4 post = make_float4(l.x + rv.x, l.y + rv.y, l.z + rv.z, l.w + rv.w);
     uint32_t nib = (post.x < 0.f) | ((post.y < 0.f) << 1) | ((post.z < 0.f) << 2) | ((post.w < 0.f) << 3);
     uint8_t *hb = a.hb1 + (static_cast<size_t>(slab) * a.n_deg1 + slot) * NB + lane0 / 8;
-    if (donenib) {  // converged lanes keep the decision of their last iteration
+    if (donenib && valid) {  // converged lanes keep the decision of their last iteration
         const float4 old = *reinterpret_cast<const float4 *>(a.post1 + base);
         if (donenib & 1) post.x = old.x;
         if (donenib & 2) post.y = old.y;
@@ -176,9 +205,9 @@ __device__ __forceinline__ void emit_deg1(const CnArgs &a, int slab, int slot, i
         const uint32_t oldnib = (static_cast<uint32_t>(*hb) >> (lane0 & 7)) & 0xFu;
         nib = (nib & ~donenib) | (oldnib & donenib);
     }
-    *reinterpret_cast<float4 *>(a.post1 + base) = post;
+    if (valid) *reinterpret_cast<float4 *>(a.post1 + base) = post;
     const uint32_t other = __shfl_xor_sync(pair_mask(), nib, 1);
-    if ((lane0 & 7) == 0) *hb = static_cast<uint8_t>(nib | (other << 4));
+    if (valid && (lane0 & 7) == 0) *hb = static_cast<uint8_t>(nib | (other << 4));
 }
 
 template <typename MsgT, int W>
@@ -193,144 +222,199 @@ __device__ __forceinline__ void store_r(const CnArgs &a, MsgT *rp, float4 rv, ui
     Msg<MsgT>::store(rp, rv);
 }
 
-template <typename MsgT, int W>
-__global__ void __launch_bounds__(kBlock) k_check_update(CnArgs a) {
+// Launch table: one entry per check class (see internal.h).  Entry k covers
+// blocks block0[k] .. block0[k+1]-1 of the grid; `deg` = dc + dd for a class
+// handled in registers, or -1 for checks read through cptr/dptr.
+constexpr int kMaxEntries = 16;
+struct ClassTable {
+    int32_t n;
+    int32_t block0[kMaxEntries + 1];
+    int32_t c0[kMaxEntries], count[kMaxEntries], dc[kMaxEntries], deg[kMaxEntries];
+    int32_t e0[kMaxEntries], s0[kMaxEntries];
+};
+
+__device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ float bitsf(uint32_t x) { return __uint_as_float(x); }
+constexpr uint32_t kSign = 0x80000000u;
+
+// Checks of one class with D = dc + dd terms, all in registers.  Every thread
+// of the warp runs this (threads past the class end work on its last check
+// and store nothing), so phi4 may vote.
+template <typename MsgT, int W, int D>
+__device__ __forceinline__ void check_regular(const CnArgs &a, const ClassTable &ct, int k,
+                                              int64_t lt, int slab) {
     constexpr int TPC = W / kK;
     constexpr int NB = W / 8;
-    const int slab = blockIdx.y;
-    if (a.et && slab_all_done<W>(a.done, slab)) return;
-    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int32_t c = static_cast<int32_t>(t / TPC);
-    if (c >= a.n_cn) return;  // both threads of a shuffle pair share c
-    const int lane0 = static_cast<int>(t % TPC) * kK;
+    const int32_t count = ct.count[k];
+    int32_t j = static_cast<int32_t>(lt / TPC);
+    const bool valid = j < count;
+    if (!valid) j = count - 1;
+    const int lane0 = static_cast<int>(lt % TPC) * kK;
+    const int dc = ct.dc[k];
+    const int32_t c = ct.c0[k] + j;
+    const int32_t e0 = ct.e0[k] + j * dc;
+    const int32_t s0 = ct.s0[k] + j * (D - dc);
+    const float lmax = a.lmax, amin = a.amin;
 
+    const uint32_t sb =
+        (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >>
+         (lane0 & 7));
+    const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
+    MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
+    const float *lvb = a.Lv + static_cast<size_t>(slab) * a.n_core * W + lane0;
+    const float *l1b = a.lch1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
+
+    int32_t vidx[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) vidx[i] = (i < dc) ? __ldg(a.col + e0 + i) : 0;
+
+    // pass 1: f = phi(|q|) carrying the sign of q in its sign bit; the top
+    // bit of par accumulates the sign parity (syndrome bit included)
+    float f[D][kK];
+    uint32_t par[kK];
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) par[kk] = ((sb >> kk) & 1u) << 31;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float4 q;
+        if (i < dc) {
+            const float4 lv = ldf4(lvb + static_cast<size_t>(vidx[i]) * W);
+            const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
+            q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
+        } else {
+            q = ldf4(l1b + static_cast<size_t>(s0 + i - dc) * W);
+        }
+        const float4 m = make_float4(clampf(fabsf(q.x), amin, lmax), clampf(fabsf(q.y), amin, lmax),
+                                     clampf(fabsf(q.z), amin, lmax), clampf(fabsf(q.w), amin, lmax));
+        const float4 ph = phi4(m);
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) {
+            const uint32_t qb = fbits(f4get(q, kk));
+            f[i][kk] = bitsf(fbits(f4get(ph, kk)) | (qb & kSign));
+            par[kk] ^= qb;
+        }
+    }
+    // exclusive prefix sums of |f|
+    float pre[D][kK];
+    {
+        float acc[kK] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) {
+                pre[i][kk] = acc[kk];
+                acc[kk] += fabsf(f[i][kk]);
+            }
+        }
+    }
+    // pass 2 (backwards): leave-one-out sum = prefix + suffix
+    float suf[kK] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = D - 1; i >= 0; --i) {
+        if (i < dc || a.final_pass) {
+            const float4 o = make_float4(clampf(pre[i][0] + suf[0], amin, lmax), clampf(pre[i][1] + suf[1], amin, lmax),
+                                         clampf(pre[i][2] + suf[2], amin, lmax), clampf(pre[i][3] + suf[3], amin, lmax));
+            const float4 m = phi4(o);
+            float4 rv;
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) {
+                const float mk = fminf(f4get(m, kk), lmax);
+                f4set(rv, kk, bitsf(fbits(mk) | ((par[kk] ^ fbits(f[i][kk])) & kSign)));
+            }
+            if (i < dc) {
+                if (valid) store_r<MsgT, W>(a, rb + static_cast<size_t>(e0 + i) * W, rv, donenib);
+            } else {
+                emit_deg1<MsgT, W>(a, slab, s0 + i - dc, lane0, rv, donenib, valid);
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) suf[kk] += fabsf(f[i][kk]);
+    }
+}
+
+// Checks of any degree, edges read through cptr/dptr; leave-one-out sums as
+// total minus own term.  Threads of a check pair stay together; nothing here
+// needs the whole warp.
+template <typename MsgT, int W>
+__device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassTable &ct, int k,
+                                                int64_t lt, int slab) {
+    constexpr int TPC = W / kK;
+    constexpr int NB = W / 8;
+    const int32_t j = static_cast<int32_t>(lt / TPC);
+    if (j >= ct.count[k]) return;
+    const int lane0 = static_cast<int>(lt % TPC) * kK;
+    const int32_t c = ct.c0[k] + j;
     const int32_t e0 = a.cptr[c], e1 = a.cptr[c + 1];
     const int32_t s0 = a.dptr[c], s1 = a.dptr[c + 1];
     const int nce = e1 - e0;
     const int deg = nce + (s1 - s0);
-    const uint32_t spar =
+    const float lmax = a.lmax, amin = a.amin;
+    const uint32_t sb =
         (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >>
-         (lane0 & 7)) & 0xFu;
+         (lane0 & 7));
     const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
-
     MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
     const float *lvb = a.Lv + static_cast<size_t>(slab) * a.n_core * W + lane0;
     const float *l1b = a.lch1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
-    const float lmax = a.lmax, amin = a.amin;
+    auto input = [&](int i) -> float4 {
+        if (i < nce) {
+            const float4 lv = ldf4(lvb + static_cast<size_t>(__ldg(a.col + e0 + i)) * W);
+            const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
+            return make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
+        }
+        return ldf4(l1b + static_cast<size_t>(s0 + i - nce) * W);
+    };
+    float S[kK] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t par[kK];
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) par[kk] = ((sb >> kk) & 1u) << 31;
+    for (int i = 0; i < deg; ++i) {
+        const float4 q = input(i);
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) {
+            const float qk = f4get(q, kk);
+            par[kk] ^= fbits(qk);
+            S[kk] += phi_f(clampf(fabsf(qk), amin, lmax));
+        }
+    }
+    for (int i = 0; i < deg; ++i) {
+        const bool out_core = i < nce;
+        if (!out_core && !a.final_pass) continue;
+        const float4 q = input(i);
+        float4 rv;
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) {
+            const float qk = f4get(q, kk);
+            const float fk = phi_f(clampf(fabsf(qk), amin, lmax));
+            const float mk = fminf(phi_f(clampf(S[kk] - fk, amin, lmax)), lmax);
+            f4set(rv, kk, bitsf(fbits(mk) | ((par[kk] ^ fbits(qk)) & kSign)));
+        }
+        if (out_core)
+            store_r<MsgT, W>(a, rb + static_cast<size_t>(e0 + i) * W, rv, donenib);
+        else
+            emit_deg1<MsgT, W>(a, slab, s0 + i - nce, lane0, rv, donenib, true);
+    }
+}
 
-    if (deg <= kMaxD) {
-        // pass 1: extrinsic inputs q, their phi and signs, kept in registers
-        float f[kMaxD][kK];
-        uint32_t neg = 0;  // bit i*4+k: q of term i, lane k is negative
-        int32_t vidx[kMaxD];
-#pragma unroll
-        for (int i = 0; i < kMaxD; ++i)
-            vidx[i] = (i < nce) ? __ldg(a.col + e0 + i) : 0;
-#pragma unroll
-        for (int i = 0; i < kMaxD; ++i) {
-            if (i < deg) {
-                float4 q;
-                if (i < nce) {
-                    const float4 lv = ldf4(lvb + static_cast<size_t>(vidx[i]) * W);
-                    const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
-                    q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
-                } else {
-                    q = ldf4(l1b + static_cast<size_t>(s0 + i - nce) * W);
-                }
-#pragma unroll
-                for (int k = 0; k < kK; ++k) {
-                    const float qk = clampf(f4get(q, k), -lmax, lmax);
-                    neg |= static_cast<uint32_t>(qk < 0.f) << (i * kK + k);
-                    f[i][k] = phi_f(clampf(fabsf(qk), amin, lmax));
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kK; ++k) f[i][k] = 0.f;
-            }
-        }
-        // total sign parity per lane, including the syndrome bit
-        uint32_t par = spar;
-#pragma unroll
-        for (int i = 0; i < kMaxD; ++i) par ^= (neg >> (i * kK)) & 0xFu;
-        // prefix sums
-        float pre[kMaxD][kK];
-        float acc[kK] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < kMaxD; ++i) {
-#pragma unroll
-            for (int k = 0; k < kK; ++k) {
-                pre[i][k] = acc[k];
-                acc[k] += f[i][k];
-            }
-        }
-        // pass 2 (backwards): leave-one-out sum = prefix + suffix
-        float suf[kK] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = kMaxD - 1; i >= 0; --i) {
-            if (i < deg) {
-                const bool out_core = i < nce;
-                if (out_core || a.final_pass) {
-                    const uint32_t sg = par ^ ((neg >> (i * kK)) & 0xFu);
-                    float4 rv;
-#pragma unroll
-                    for (int k = 0; k < kK; ++k) {
-                        const float m = fminf(phi_f(clampf(pre[i][k] + suf[k], amin, lmax)), lmax);
-                        f4set(rv, k, ((sg >> k) & 1u) ? -m : m);
-                    }
-                    if (out_core)
-                        store_r<MsgT, W>(a, rb + static_cast<size_t>(e0 + i) * W, rv, donenib);
-                    else
-                        emit_deg1<MsgT, W>(a, slab, s0 + i - nce, lane0, rv, donenib);
-                }
-#pragma unroll
-                for (int k = 0; k < kK; ++k) suf[k] += f[i][k];
-            }
-        }
-    } else {
-        // high-degree check: two streaming passes, leave-one-out as total - own
-        float S[kK] = {0.f, 0.f, 0.f, 0.f};
-        uint32_t par = spar;
-        for (int i = 0; i < deg; ++i) {
-            float4 q;
-            if (i < nce) {
-                const float4 lv = ldf4(lvb + static_cast<size_t>(__ldg(a.col + e0 + i)) * W);
-                const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
-                q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
-            } else {
-                q = ldf4(l1b + static_cast<size_t>(s0 + i - nce) * W);
-            }
-#pragma unroll
-            for (int k = 0; k < kK; ++k) {
-                const float qk = clampf(f4get(q, k), -lmax, lmax);
-                par ^= static_cast<uint32_t>(qk < 0.f) << k;
-                S[k] += phi_f(clampf(fabsf(qk), amin, lmax));
-            }
-        }
-        for (int i = 0; i < deg; ++i) {
-            const bool out_core = i < nce;
-            if (!out_core && !a.final_pass) continue;
-            float4 q;
-            if (out_core) {
-                const float4 lv = ldf4(lvb + static_cast<size_t>(__ldg(a.col + e0 + i)) * W);
-                const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
-                q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
-            } else {
-                q = ldf4(l1b + static_cast<size_t>(s0 + i - nce) * W);
-            }
-            float4 rv;
-#pragma unroll
-            for (int k = 0; k < kK; ++k) {
-                const float qk = clampf(f4get(q, k), -lmax, lmax);
-                const float fk = phi_f(clampf(fabsf(qk), amin, lmax));
-                const uint32_t sg = ((par >> k) & 1u) ^ static_cast<uint32_t>(qk < 0.f);
-                const float m = fminf(phi_f(clampf(S[k] - fk, amin, lmax)), lmax);
-                f4set(rv, k, sg ? -m : m);
-            }
-            if (out_core)
-                store_r<MsgT, W>(a, rb + static_cast<size_t>(e0 + i) * W, rv, donenib);
-            else
-                emit_deg1<MsgT, W>(a, slab, s0 + i - nce, lane0, rv, donenib);
-        }
+// DMAX: the largest register-held degree in the table (4, 6 or 8); smaller
+// tables compile to smaller register arrays and higher occupancy.
+template <typename MsgT, int W, int DMAX>
+__global__ void __launch_bounds__(kBlock, (DMAX <= 6 ? 4 : 2)) k_check_update(CnArgs a, ClassTable ct) {
+    const int slab = blockIdx.y;
+    if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
+    int k = 0;
+    while (k + 1 < ct.n && static_cast<int32_t>(blockIdx.x) >= ct.block0[k + 1]) ++k;
+    const int64_t lt = static_cast<int64_t>(blockIdx.x - ct.block0[k]) * blockDim.x + threadIdx.x;
+    switch (ct.deg[k]) {
+        case 1: check_regular<MsgT, W, 1>(a, ct, k, lt, slab); break;
+        case 2: check_regular<MsgT, W, 2>(a, ct, k, lt, slab); break;
+        case 3: check_regular<MsgT, W, 3>(a, ct, k, lt, slab); break;
+        case 4: check_regular<MsgT, W, 4>(a, ct, k, lt, slab); break;
+        case 5: if constexpr (DMAX >= 5) check_regular<MsgT, W, 5>(a, ct, k, lt, slab); break;
+        case 6: if constexpr (DMAX >= 6) check_regular<MsgT, W, 6>(a, ct, k, lt, slab); break;
+        case 7: if constexpr (DMAX >= 7) check_regular<MsgT, W, 7>(a, ct, k, lt, slab); break;
+        case 8: if constexpr (DMAX >= 8) check_regular<MsgT, W, 8>(a, ct, k, lt, slab); break;
+        default: check_irregular<MsgT, W>(a, ct, k, lt, slab); break;
     }
 }
 
@@ -477,7 +561,7 @@ __global__ void __launch_bounds__(kBlock) k_interleave_in(InArgs a) {
                 const float s = a.sigma[b];
                 v = (s > 0.f) ? v * (2.0f / (s * s)) : 0.f;
             }
-            v = clampf(v, -a.lmax, a.lmax);
+            v = clampf(v, -a.lmax, a.lmax) + 0.0f;  // -0 -> +0: a zero LLR has no sign
         }
         tile[w][jj] = v;
     }
@@ -501,12 +585,12 @@ __global__ void __launch_bounds__(kBlock) k_interleave_in(InArgs a) {
 }
 
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_syndrome_in(const uint8_t *syn, int32_t n_cn, int32_t batch,
-                                                        uint8_t *sbits) {
+__global__ void __launch_bounds__(kBlock) k_syndrome_in(const uint8_t *syn, const int32_t *cint, int32_t n_cn,
+                                                        int32_t batch, uint8_t *sbits) {
     constexpr int NB = W / 8;
     __shared__ uint8_t tile[W][33];
     const int slab = blockIdx.y;
-    const int32_t c0 = blockIdx.x * 32;
+    const int32_t c0 = blockIdx.x * 32;  // caller's check order (coalesced reads)
     for (int idx = threadIdx.x; idx < W * 32; idx += blockDim.x) {
         const int w = idx / 32, cc = idx % 32;
         const int b = slab * W + w;
@@ -521,7 +605,7 @@ __global__ void __launch_bounds__(kBlock) k_syndrome_in(const uint8_t *syn, int3
         uint32_t byte = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) byte |= static_cast<uint32_t>(tile[g * 8 + k][cc]) << k;
-        sbits[(static_cast<size_t>(slab) * n_cn + c) * NB + g] = static_cast<uint8_t>(byte);
+        sbits[(static_cast<size_t>(slab) * n_cn + cint[c]) * NB + g] = static_cast<uint8_t>(byte);
     }
 }
 
@@ -746,7 +830,8 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     }
     if (h.n_cn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_syndrome_in", [&] {
-            k_syndrome_in<W><<<dim3((h.n_cn + 31) / 32, slabs), kBlock, 0, st>>>(syn, h.n_cn, batch, d->sbits);
+            k_syndrome_in<W><<<dim3((h.n_cn + 31) / 32, slabs), kBlock, 0, st>>>(syn, g->cint, h.n_cn, batch,
+                                                                                d->sbits);
         });
         if (s != MLD_OK) return s;
     }
@@ -757,7 +842,33 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
                d->fail, d->done, et ? 1 : 0};
-    const dim3 cn_grid(grid_x(static_cast<int64_t>(h.n_cn) * TPC), slabs);
+    // launch tables for the check classes
+    std::vector<ClassTable> tables;
+    {
+        ClassTable t{};
+        for (const mld::CheckClass &cl : h.classes) {
+            if (cl.dc == 0 && cl.dd == 0) continue;  // checks without edges: nothing to send
+            if (t.n == kMaxEntries) {
+                tables.push_back(t);
+                t = ClassTable{};
+            }
+            const int i = t.n++;
+            t.c0[i] = cl.c0;
+            t.count[i] = cl.count;
+            t.dc[i] = cl.dc;
+            t.deg[i] = cl.dc < 0 ? -1 : cl.dc + cl.dd;
+            t.e0[i] = cl.e0;
+            t.s0[i] = cl.s0;
+            t.block0[i + 1] = t.block0[i] + grid_x(static_cast<int64_t>(cl.count) * TPC);
+        }
+        if (t.n > 0) tables.push_back(t);
+    }
+    std::vector<int> table_dmax;
+    for (const ClassTable &t : tables) {
+        int m = 0;
+        for (int i = 0; i < t.n; ++i) m = std::max(m, t.deg[i]);
+        table_dmax.push_back(m);
+    }
     const dim3 vn_grid(grid_x(static_cast<int64_t>(h.n_core) * TPC), slabs);
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, d->device);
@@ -802,9 +913,16 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     for (int32_t l = 1; l <= iters; ++l) {
         const bool last = (l == iters);
         ca.final_pass = (last || et) ? 1 : 0;
-        if (h.n_cn > 0 && (h.e_core > 0 || h.n_deg1 > 0)) {
+        for (size_t ti = 0; ti < tables.size(); ++ti) {
+            const ClassTable &t = tables[ti];
+            const dim3 grid(t.block0[t.n], slabs);
             int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
-                k_check_update<MsgT, W><<<cn_grid, kBlock, 0, st>>>(ca);
+                if (table_dmax[ti] <= 4)
+                    k_check_update<MsgT, W, 4><<<grid, kBlock, 0, st>>>(ca, t);
+                else if (table_dmax[ti] <= 6)
+                    k_check_update<MsgT, W, 6><<<grid, kBlock, 0, st>>>(ca, t);
+                else
+                    k_check_update<MsgT, W, 8><<<grid, kBlock, 0, st>>>(ca, t);
             });
             if (s != MLD_OK) return s;
         }
@@ -926,6 +1044,11 @@ int mld_graph_create(const int32_t *edge_vn, const int32_t *edge_cn, const uint8
     if (s == MLD_OK) s = upload(&g->vptr, g->h.vptr);
     if (s == MLD_OK) s = upload(&g->vedge, g->h.vedge);
     if (s == MLD_OK) s = upload(&g->unit, g->h.unit);
+    if (s == MLD_OK) {
+        std::vector<int32_t> cint(g->h.n_cn);
+        for (int32_t i = 0; i < g->h.n_cn; ++i) cint[g->h.cuser[i]] = i;
+        s = upload(&g->cint, cint);
+    }
     if (s == MLD_OK) s = upload(&g->etype_core, g->h.etype_core);
     if (s == MLD_OK) s = upload(&g->etype_deg1, g->h.etype_deg1);
     if (s != MLD_OK) {
@@ -939,7 +1062,7 @@ int mld_graph_create(const int32_t *edge_vn, const int32_t *edge_cn, const uint8
 int mld_graph_destroy(mld_graph *g) {
     if (!g) return MLD_OK;
     dfree(g->cptr); dfree(g->col); dfree(g->dptr); dfree(g->vptr); dfree(g->vedge);
-    dfree(g->unit); dfree(g->etype_core); dfree(g->etype_deg1);
+    dfree(g->unit); dfree(g->cint); dfree(g->etype_core); dfree(g->etype_deg1);
     delete g;
     return MLD_OK;
 }

@@ -71,17 +71,32 @@ int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
     for (int32_t v = 0; v < n_vn; ++v)
         if (core_id[v] >= 0) g.unit[v] = core_id[v];
 
+    // edges of each caller check in `order`, and its (dc, dd) class key
+    std::vector<int64_t> ustart(static_cast<size_t>(n_cn) + 1, 0);
+    for (int32_t c = 0; c < n_cn; ++c) ustart[c + 1] = ustart[c] + cdeg[c];
+    std::vector<int32_t> dcs(n_cn, 0), dds(n_cn, 0);
+    for (int64_t k = 0; k < n_edges; ++k) {
+        if (core_id[edge_vn[k]] >= 0) dcs[edge_cn[k]]++;
+        else dds[edge_cn[k]]++;
+    }
+    auto key = [&](int32_t c) -> int64_t {
+        return (dcs[c] + dds[c] <= kMaxRegDeg) ? static_cast<int64_t>(dcs[c]) * 64 + dds[c] : (1LL << 40);
+    };
+    g.cuser.resize(n_cn);
+    std::iota(g.cuser.begin(), g.cuser.end(), 0);
+    std::stable_sort(g.cuser.begin(), g.cuser.end(), [&](int32_t a, int32_t b) { return key(a) < key(b); });
+
     g.cptr.assign(static_cast<size_t>(n_cn) + 1, 0);
     g.dptr.assign(static_cast<size_t>(n_cn) + 1, 0);
     g.col.resize(g.e_core);
     g.etype_core.resize(g.e_core);
     g.etype_deg1.resize(g.n_deg1);
     int32_t ce = 0, slot = 0;
-    int64_t i = 0;
-    for (int32_t c = 0; c < n_cn; ++c) {
-        g.cptr[c] = ce;
-        g.dptr[c] = slot;
-        for (; i < n_edges && edge_cn[order[i]] == c; ++i) {
+    for (int32_t ci = 0; ci < n_cn; ++ci) {
+        const int32_t c = g.cuser[ci];
+        g.cptr[ci] = ce;
+        g.dptr[ci] = slot;
+        for (int64_t i = ustart[c]; i < ustart[c + 1]; ++i) {
             const int32_t k = order[i];
             const int32_t v = edge_vn[k];
             const uint8_t t = edge_type ? edge_type[k] : 0;
@@ -96,11 +111,24 @@ int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
             }
         }
         g.max_check_deg = std::max(g.max_check_deg, cdeg[c]);
+        // open a new class when the key changes
+        const bool regular = dcs[c] + dds[c] <= kMaxRegDeg;
+        if (g.classes.empty() || key(c) != key(g.cuser[g.classes.back().c0])) {
+            CheckClass cl;
+            cl.c0 = ci;
+            cl.count = 0;
+            cl.dc = regular ? dcs[c] : -1;
+            cl.dd = regular ? dds[c] : -1;
+            cl.e0 = g.cptr[ci];
+            cl.s0 = g.dptr[ci];
+            g.classes.push_back(cl);
+        }
+        g.classes.back().count++;
     }
     g.cptr[n_cn] = ce;
     g.dptr[n_cn] = slot;
-    // (core edges of a check are already ascending in core id because the
-    // natural order is ascending and core ids preserve it)
+    // (core edges of a check are ascending in core id: `order` is ascending in
+    // VN and core ids preserve the natural order)
 
     // VN-major view of the core edges
     g.vptr.assign(static_cast<size_t>(g.n_core) + 1, 0);

@@ -28,13 +28,29 @@ void clear_error();
 //    vedge[vptr[v]..vptr[v+1]], ascending.
 //  * unit[j] maps natural VN j to its internal index: core VN index, or
 //    n_core + slot for a degree-1 VN.
+//  * Checks are renumbered so that checks with the same number of core edges
+//    (dc) and degree-1 VNs (dd) are contiguous ("classes").  Inside a class
+//    with dc + dd <= kMaxRegDeg the edge range of a check is computed from its
+//    position (e0 + j*dc, s0 + j*dd) instead of loaded.  Checks of higher
+//    degree form one irregular class (dc = -1) that uses cptr/dptr.
+//    cuser[c] is the caller's index of internal check c (cint is its inverse,
+//    kept on the device to scatter syndrome bits into internal order).
+constexpr int kMaxRegDeg = 8;
+
+struct CheckClass {
+    int32_t c0, count;  // internal checks c0 .. c0+count-1
+    int32_t dc, dd;     // core edges and degree-1 VNs per check (dc = -1: irregular)
+    int32_t e0, s0;     // first core edge and first degree-1 slot of the class
+};
+
 struct HostGraph {
     int32_t n_vn = 0, n_cn = 0;
     int64_t n_edges = 0;
     int32_t n_core = 0, n_deg1 = 0;
     int32_t e_core = 0;
     int32_t max_check_deg = 0, max_vn_deg = 0;
-    std::vector<int32_t> cptr, col, dptr, vptr, vedge, unit;
+    std::vector<int32_t> cptr, col, dptr, vptr, vedge, unit, cuser;
+    std::vector<CheckClass> classes;
     std::vector<uint8_t> etype_core, etype_deg1;
 };
 
@@ -49,6 +65,6 @@ struct mld_graph {
     int device = 0;
     // device copies of the index arrays
     int32_t *cptr = nullptr, *col = nullptr, *dptr = nullptr;
-    int32_t *vptr = nullptr, *vedge = nullptr, *unit = nullptr;
+    int32_t *vptr = nullptr, *vedge = nullptr, *unit = nullptr, *cint = nullptr;
     uint8_t *etype_core = nullptr, *etype_deg1 = nullptr;
 };
