@@ -45,7 +45,7 @@ constexpr int kBlock = 256;
 // ---------------------------------------------------------------------------
 // phi(x) = -ln tanh(x/2) in float, for x in [phi(lmax), lmax].
 // Two pieces (see gen_phi_poly.py): below MLD_PHI_X0, ln2 - ln x - t Ps(t)
-// with t = x^2; above, 2 e Pl(e^2) with e = exp(-x).  ln and exp come from
+// with t = x^2; above, e Pl(e^2) with e = exp(-x).  ln and exp come from
 // the MUFU base-2 approximations.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float mufu_lg2(float x) {
@@ -76,7 +76,7 @@ __device__ __forceinline__ float phi_large(float x) {
     float pl = fmaf(MLD_PHI_L3, z, MLD_PHI_L2);
     pl = fmaf(pl, z, MLD_PHI_L1);
     pl = fmaf(pl, z, MLD_PHI_L0);
-    return (e + e) * pl;
+    return e * pl;
 }
 
 // Branch-free choice x < th ? a : b (both operands are already computed).
@@ -96,15 +96,23 @@ __device__ __forceinline__ float phi_f(float x) {
 // needs it (one MUFU op per value instead of two when the warp agrees); the
 // result equals phi_f element by element.  Must be called by all 32 lanes.
 __device__ __forceinline__ float4 phi4(float4 x) {
-    const bool any_s = (x.x < MLD_PHI_X0) | (x.y < MLD_PHI_X0) | (x.z < MLD_PHI_X0) | (x.w < MLD_PHI_X0);
-    const bool any_l = !((x.x < MLD_PHI_X0) & (x.y < MLD_PHI_X0) & (x.z < MLD_PHI_X0) & (x.w < MLD_PHI_X0));
-    float4 sm = make_float4(0.f, 0.f, 0.f, 0.f), lg = sm;
-    if (__any_sync(0xFFFFFFFFu, any_s))
-        sm = make_float4(phi_small(x.x), phi_small(x.y), phi_small(x.z), phi_small(x.w));
-    if (__any_sync(0xFFFFFFFFu, any_l))
-        lg = make_float4(phi_large(x.x), phi_large(x.y), phi_large(x.z), phi_large(x.w));
-    return make_float4(sel_lt(x.x, MLD_PHI_X0, sm.x, lg.x), sel_lt(x.y, MLD_PHI_X0, sm.y, lg.y),
-                       sel_lt(x.z, MLD_PHI_X0, sm.z, lg.z), sel_lt(x.w, MLD_PHI_X0, sm.w, lg.w));
+    const float mn = fminf(fminf(x.x, x.y), fminf(x.z, x.w));
+    const float mx = fmaxf(fmaxf(x.x, x.y), fmaxf(x.z, x.w));
+    const bool need_s = __any_sync(0xFFFFFFFFu, mn < MLD_PHI_X0);
+    const bool need_l = __any_sync(0xFFFFFFFFu, mx >= MLD_PHI_X0);
+    float4 r;
+    if (need_l) {
+        r = make_float4(phi_large(x.x), phi_large(x.y), phi_large(x.z), phi_large(x.w));
+        if (need_s) {
+            r.x = sel_lt(x.x, MLD_PHI_X0, phi_small(x.x), r.x);
+            r.y = sel_lt(x.y, MLD_PHI_X0, phi_small(x.y), r.y);
+            r.z = sel_lt(x.z, MLD_PHI_X0, phi_small(x.z), r.z);
+            r.w = sel_lt(x.w, MLD_PHI_X0, phi_small(x.w), r.w);
+        }
+    } else {
+        r = make_float4(phi_small(x.x), phi_small(x.y), phi_small(x.z), phi_small(x.w));
+    }
+    return r;
 }
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
@@ -312,15 +320,18 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassTable 
 #pragma unroll
     for (int i = D - 1; i >= 0; --i) {
         if (i < dc || a.final_pass) {
-            const float4 o = make_float4(clampf(pre[i][0] + suf[0], amin, lmax), clampf(pre[i][1] + suf[1], amin, lmax),
-                                         clampf(pre[i][2] + suf[2], amin, lmax), clampf(pre[i][3] + suf[3], amin, lmax));
-            const float4 m = phi4(o);
+            // every other term contributes phi(|q|) >= phi(lmax) ~ amin, so for
+            // D >= 2 the sum is already >= amin (up to rounding) and for D >= 3
+            // phi of it stays below lmax; only the needed clamps are applied
+            float4 o = make_float4(fminf(pre[i][0] + suf[0], lmax), fminf(pre[i][1] + suf[1], lmax),
+                                   fminf(pre[i][2] + suf[2], lmax), fminf(pre[i][3] + suf[3], lmax));
+            if (D == 1) o = make_float4(amin, amin, amin, amin);
+            float4 m = phi4(o);
+            if (D <= 2) m = make_float4(fminf(m.x, lmax), fminf(m.y, lmax), fminf(m.z, lmax), fminf(m.w, lmax));
             float4 rv;
 #pragma unroll
-            for (int kk = 0; kk < kK; ++kk) {
-                const float mk = fminf(f4get(m, kk), lmax);
-                f4set(rv, kk, bitsf(fbits(mk) | ((par[kk] ^ fbits(f[i][kk])) & kSign)));
-            }
+            for (int kk = 0; kk < kK; ++kk)
+                f4set(rv, kk, bitsf(fbits(f4get(m, kk)) | ((par[kk] ^ fbits(f[i][kk])) & kSign)));
             if (i < dc) {
                 if (valid) store_r<MsgT, W>(a, rb + static_cast<size_t>(e0 + i) * W, rv, donenib);
             } else {

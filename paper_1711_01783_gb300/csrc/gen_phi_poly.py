@@ -7,8 +7,8 @@ degrees change; its output is committed).  The device evaluates phi on
   x <  X0 :  phi(x) = ln 2 - ln(x) - t * Ps(t),      t = x^2
              where t * Ps(t) approximates h(x) = ln(tanh(x/2) / (x/2)),
              an even function analytic for |x| < pi;
-  x >= X0 :  phi(x) = 2 atanh(e) = 2 e * Pl(e^2),    e = exp(-x)
-             where Pl(z) approximates atanh(sqrt z) / sqrt z.
+  x >= X0 :  phi(x) = 2 atanh(e) = e * Pl(e^2),      e = exp(-x)
+             where Pl(z) approximates 2 atanh(sqrt z) / sqrt z.
 
 ln(x) and exp(-x) come from the hardware base-2 approximations (MUFU lg2 /
 ex2).  The coefficients are least-squares fits on Chebyshev nodes of the
@@ -36,7 +36,7 @@ def fit():
     err_s = np.max(np.abs(np.polynomial.polynomial.polyval(t, cs) * t - h))
     z = _cheb(1e-14, np.exp(-2 * X0))
     e = np.sqrt(z)
-    pl = np.arctanh(e) / e
+    pl = 2.0 * np.arctanh(e) / e
     cl = np.polynomial.polynomial.polyfit(z, pl, DEG_LARGE - 1)
     err_l = np.max(np.abs(np.polynomial.polynomial.polyval(z, cl) / pl - 1))
     return cs, cl, err_s, err_l
@@ -48,7 +48,7 @@ def main():
     lines = [
         "// Generated by gen_phi_poly.py -- polynomial pieces of phi(x) = -ln tanh(x/2).",
         f"// small branch x < {X0}: phi = ln2 - ln x - t*Ps(t), t = x^2; max |fit error| {err_s:.2e}",
-        f"// large branch: phi = 2e*Pl(e^2), e = exp(-x); max relative fit error {err_l:.2e}",
+        f"// large branch: phi = e*Pl(e^2), e = exp(-x); max relative fit error {err_l:.2e}",
         "#pragma once",
         f"#define MLD_PHI_X0 {X0:.9g}f",
     ]

@@ -1,6 +1,6 @@
 // Generated by gen_phi_poly.py -- polynomial pieces of phi(x) = -ln tanh(x/2).
 // small branch x < 1.25: phi = ln2 - ln x - t*Ps(t), t = x^2; max |fit error| 3.38e-09
-// large branch: phi = 2e*Pl(e^2), e = exp(-x); max relative fit error 4.63e-08
+// large branch: phi = e*Pl(e^2), e = exp(-x); max relative fit error 4.63e-08
 #pragma once
 #define MLD_PHI_X0 1.25f
 #define MLD_PHI_S0 (-8.333333104e-02f)
@@ -8,7 +8,7 @@
 #define MLD_PHI_S2 (-3.413196527e-04f)
 #define MLD_PHI_S3 (2.552129118e-05f)
 #define MLD_PHI_S4 (-1.561553869e-06f)
-#define MLD_PHI_L0 (9.999999540e-01f)
-#define MLD_PHI_L1 (3.333511153e-01f)
-#define MLD_PHI_L2 (1.989340331e-01f)
-#define MLD_PHI_L3 (1.629801372e-01f)
+#define MLD_PHI_L0 (1.999999908e+00f)
+#define MLD_PHI_L1 (6.667022306e-01f)
+#define MLD_PHI_L2 (3.978680662e-01f)
+#define MLD_PHI_L3 (3.259602744e-01f)
