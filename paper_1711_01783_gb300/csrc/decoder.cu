@@ -230,16 +230,8 @@ __device__ __forceinline__ void store_r(const CnArgs &a, MsgT *rp, float4 rv, ui
     Msg<MsgT>::store(rp, rv);
 }
 
-// Launch table: one entry per check class (see internal.h).  Entry k covers
-// blocks block0[k] .. block0[k+1]-1 of the grid; `deg` = dc + dd for a class
-// handled in registers, or -1 for checks read through cptr/dptr.
-constexpr int kMaxEntries = 16;
-struct ClassTable {
-    int32_t n;
-    int32_t block0[kMaxEntries + 1];
-    int32_t c0[kMaxEntries], count[kMaxEntries], dc[kMaxEntries], deg[kMaxEntries];
-    int32_t e0[kMaxEntries], s0[kMaxEntries];
-};
+using mld::ClassTable;
+using mld::kMaxEntries;
 
 __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
 __device__ __forceinline__ float bitsf(uint32_t x) { return __uint_as_float(x); }
@@ -731,6 +723,40 @@ int grid_x(int64_t threads) {
 
 }  // namespace
 
+// Launch tables of the check update for each slab width: one entry per check
+// class, entries grouped kMaxEntries to a launch.
+void build_class_tables(mld_graph *g) {
+    const int widths[4] = {8, 16, 32, 64};
+    for (int wi = 0; wi < 4; ++wi) {
+        const int tpc = widths[wi] / kK;
+        std::vector<ClassTable> &tables = g->tables[wi];
+        tables.clear();
+        ClassTable t{};
+        for (const mld::CheckClass &cl : g->h.classes) {
+            if (cl.dc == 0 && cl.dd == 0) continue;  // checks without edges: nothing to send
+            if (t.n == kMaxEntries) {
+                tables.push_back(t);
+                t = ClassTable{};
+            }
+            const int i = t.n++;
+            t.c0[i] = cl.c0;
+            t.count[i] = cl.count;
+            t.dc[i] = cl.dc;
+            t.deg[i] = cl.dc < 0 ? -1 : cl.dc + cl.dd;
+            t.e0[i] = cl.e0;
+            t.s0[i] = cl.s0;
+            t.block0[i + 1] = t.block0[i] + grid_x(static_cast<int64_t>(cl.count) * tpc);
+        }
+        if (t.n > 0) tables.push_back(t);
+        g->table_dmax[wi].clear();
+        for (const ClassTable &tt : tables) {
+            int m = 0;
+            for (int i = 0; i < tt.n; ++i) m = std::max(m, tt.deg[i]);
+            g->table_dmax[wi].push_back(m);
+        }
+    }
+}
+
 // ===========================================================================
 // decoder object
 // ===========================================================================
@@ -853,33 +879,10 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
                d->fail, d->done, et ? 1 : 0};
-    // launch tables for the check classes
-    std::vector<ClassTable> tables;
-    {
-        ClassTable t{};
-        for (const mld::CheckClass &cl : h.classes) {
-            if (cl.dc == 0 && cl.dd == 0) continue;  // checks without edges: nothing to send
-            if (t.n == kMaxEntries) {
-                tables.push_back(t);
-                t = ClassTable{};
-            }
-            const int i = t.n++;
-            t.c0[i] = cl.c0;
-            t.count[i] = cl.count;
-            t.dc[i] = cl.dc;
-            t.deg[i] = cl.dc < 0 ? -1 : cl.dc + cl.dd;
-            t.e0[i] = cl.e0;
-            t.s0[i] = cl.s0;
-            t.block0[i + 1] = t.block0[i] + grid_x(static_cast<int64_t>(cl.count) * TPC);
-        }
-        if (t.n > 0) tables.push_back(t);
-    }
-    std::vector<int> table_dmax;
-    for (const ClassTable &t : tables) {
-        int m = 0;
-        for (int i = 0; i < t.n; ++i) m = std::max(m, t.deg[i]);
-        table_dmax.push_back(m);
-    }
+    // launch tables for the check classes (built with the graph)
+    const int wi = W == 8 ? 0 : (W == 16 ? 1 : (W == 32 ? 2 : 3));
+    const std::vector<ClassTable> &tables = g->tables[wi];
+    const std::vector<int> &table_dmax = g->table_dmax[wi];
     const dim3 vn_grid(grid_x(static_cast<int64_t>(h.n_core) * TPC), slabs);
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, d->device);
@@ -1066,6 +1069,7 @@ int mld_graph_create(const int32_t *edge_vn, const int32_t *edge_cn, const uint8
         mld_graph_destroy(g);
         return s;
     }
+    build_class_tables(g);
     *out = g;
     return MLD_OK;
 }
@@ -1231,3 +1235,4 @@ int mld_phi_eval(const float *x, float *out, int64_t n, void *stream) {
 }
 
 }  // extern "C"
+
