@@ -189,6 +189,49 @@ typedef struct {
 int mld_decoder_timing_enable(mld_decoder *d, int enable);
 int mld_decoder_timing_read(mld_decoder *d, mld_timing *out);
 
+/* ---- decoding without any device allocation ------------------------------
+ * (The paper has no counterpart to this entry point: it concerns how the
+ * library obtains memory, not the decoding method.)
+ *
+ * mld_decode_noalloc decodes like mld_decode, but without a decoder object
+ * and without allocating anything: its working memory (messages, posteriors,
+ * interleaved inputs, syndrome and decision bits, per-codeword flags) is
+ * carved from one file-scope device array of MLD_NOALLOC_SCRATCH_BYTES that
+ * the library reserves on every GPU it is loaded on, for the life of the
+ * process.  It serves callers that cannot call cudaMalloc: hosts whose device
+ * memory is owned entirely by their own allocator or capped at start-up (a
+ * framework's caching pool, a fixed real-time budget), and code paths where
+ * an allocation is not allowed or where the implicit device synchronisation
+ * of cudaMalloc/cudaFree would stall other streams.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   g          : a graph from mld_graph_create (created beforehand).
+ *   msg_dtype  : MLD_MSG_F32 (slabs of 32 codewords) or MLD_MSG_F16 (64).
+ *   llr, syndrome, bits_out, post_out (or NULL), converged, iters_used:
+ *                DEVICE pointers laid out as for mld_decode; the call reads
+ *                and writes only these and the scratch array.  MLD_DEVICE_PTRS
+ *                may be given in flags and is implied.
+ *   flags      : MLD_EARLY_TERM and/or MLD_DEVICE_PTRS.
+ * The LLR clamp is 25.  Results are those of mld_decode with the same graph,
+ * dtype, default slab width and inputs.
+ * Limit: the working set for (graph, batch, msg_dtype) must fit in
+ * MLD_NOALLOC_SCRATCH_BYTES; otherwise the call returns MLD_EINVAL and
+ * mld_last_error() states the bytes needed.  (A rate-0.1 graph with n = 4096
+ * needs about 4.5 MiB per slab of 64 codewords with half messages.)
+ * Set-up: the first call on each device, made with that device current,
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it;
+ * make that first call before any stream capture on the device.
+ * Sharing: every call on a device uses the same array, which keeps the last
+ * call's contents; each call clears what must start at zero.  Calls whose
+ * work overlaps on the GPU (different streams, or host threads racing)
+ * corrupt each other: serialize them.
+ * Errors: MLD_EINVAL (null pointer, bad dtype/flag/size, scratch too small),
+ * MLD_ECUDA. */
+#define MLD_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int mld_decode_noalloc(const mld_graph *g, int32_t msg_dtype, const float *llr,
+                       const uint8_t *syndrome, int32_t batch, int32_t max_iters,
+                       uint32_t flags, uint8_t *bits_out, float *post_out,
+                       uint8_t *converged, int32_t *iters_used, void *stream);
+
 /* ---- phi evaluation (verification hook) ----------------------------------
  * Evaluates on the device the float phi(x) = -ln tanh(x/2) that the check
  * update uses (the LLR-domain message map that the closing paragraph of the

@@ -32,7 +32,7 @@ _STATUS = {MLD_EINVAL: "MLD_EINVAL", MLD_ENOMEM: "MLD_ENOMEM", MLD_ECUDA: "MLD_E
 EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destroy",
            "mld_graph_stats_get", "mld_decoder_create", "mld_decoder_destroy", "mld_decode",
            "mld_decode_y", "mld_decode_status", "mld_decoder_timing_enable",
-           "mld_decoder_timing_read", "mld_phi_eval")
+           "mld_decoder_timing_read", "mld_decode_noalloc", "mld_phi_eval")
 
 
 class MldError(RuntimeError):
@@ -79,6 +79,7 @@ def _load() -> ctypes.CDLL:
         "mld_decode_status": (ctypes.c_int, [P]),
         "mld_decoder_timing_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "mld_decoder_timing_read": (ctypes.c_int, [P, ctypes.POINTER(Timing)]),
+        "mld_decode_noalloc": (ctypes.c_int, [P, I32, P, P, I32, I32, U32, P, P, P, P, P]),
         "mld_phi_eval": (ctypes.c_int, [P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
@@ -276,6 +277,31 @@ class Decoder:
         return {f: getattr(t, f) for f, _ in Timing._fields_}
 
 
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def decode_noalloc(graph: Graph, llr, syndrome, iters: int, msg_dtype: str = "f32",
+                   early_term: bool = False, want_post: bool = False, stream=None):
+    """Decode without a decoder object and without allocating device memory
+    in the library (mld_decode_noalloc).  Inputs are CUDA tensors; the output
+    tensors are allocated here by torch, the library allocates nothing."""
+    torch = _torch()
+    llr = llr.contiguous()
+    syndrome = syndrome.contiguous().to(torch.uint8)
+    B, n = int(llr.shape[0]), graph.n_vn
+    dev = llr.device
+    out = dict(bits=torch.empty((B, n), dtype=torch.uint8, device=dev),
+               post=torch.empty((B, n), dtype=torch.float32, device=dev) if want_post else None,
+               converged=torch.empty(B, dtype=torch.uint8, device=dev),
+               iters_used=torch.empty(B, dtype=torch.int32, device=dev))
+    flags = (MLD_EARLY_TERM if early_term else 0) | MLD_DEVICE_PTRS
+    dt = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
+    _check(lib().mld_decode_noalloc(graph.handle, dt, _ptr(llr), _ptr(syndrome), B, int(iters), flags,
+                                    _ptr(out["bits"]), _ptr(out["post"]), _ptr(out["converged"]),
+                                    _ptr(out["iters_used"]), _stream_handle(stream)))
+    return out
+
+
 def phi(x, stream=None):
     """Device phi(x) = -ln tanh(x/2) as used by the check update (float32 CUDA tensor)."""
     torch = _torch()
@@ -285,4 +311,5 @@ def phi(x, stream=None):
     return out
 
 
-__all__ = ["Graph", "Decoder", "phi", "version", "lib", "MldError", "EXPORTS", "LIB_PATH"]
+__all__ = ["Graph", "Decoder", "phi", "decode_noalloc", "version", "lib", "MldError", "EXPORTS",
+           "LIB_PATH", "NOALLOC_SCRATCH_BYTES"]

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1236,3 +1237,122 @@ int mld_phi_eval(const float *x, float *out, int64_t n, void *stream) {
 
 }  // extern "C"
 
+// ===========================================================================
+// Allocation-free decode: working memory in a file-scope device array
+// ===========================================================================
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[MLD_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device `dev`.  In host
+// code the array's name is only a host-side stand-in, so the address is looked
+// up once per device and cached.
+int noalloc_base(int dev, void **out) {
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return mld::fail(MLD_EINVAL, "decode_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return MLD_OK;
+}
+
+// Offsets of the working buffers inside the scratch array (256-byte aligned).
+struct NoallocLayout {
+    size_t r, Lv, lch, lch1, post1, hb_core, hb1, sbits, done, fail, iters, conv, total;
+};
+
+NoallocLayout noalloc_layout(const mld::HostGraph &h, int W, size_t msz, int slabs) {
+    NoallocLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (std::max<size_t>(bytes, 1) + 255) & ~static_cast<size_t>(255);
+        return o;
+    };
+    const size_t S = static_cast<size_t>(slabs);
+    const size_t NB = W / 8, DW = (W + 31) / 32;
+    L.r = take(S * h.e_core * W * msz);
+    L.Lv = take(S * h.n_core * W * sizeof(float));
+    L.lch = take(S * h.n_core * W * sizeof(float));
+    L.lch1 = take(S * h.n_deg1 * W * sizeof(float));
+    L.post1 = take(S * h.n_deg1 * W * sizeof(float));
+    L.hb_core = take(S * h.n_core * NB);
+    L.hb1 = take(S * h.n_deg1 * NB);
+    L.sbits = take(S * h.n_cn * NB);
+    L.done = take(S * DW * sizeof(uint32_t));
+    L.fail = take(S * DW * sizeof(uint32_t));
+    L.iters = take(S * W * sizeof(int32_t));
+    L.conv = take(S * W);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+extern "C" int mld_decode_noalloc(const mld_graph *g, int32_t msg_dtype, const float *llr,
+                                  const uint8_t *syndrome, int32_t batch, int32_t max_iters,
+                                  uint32_t flags, uint8_t *bits_out, float *post_out,
+                                  uint8_t *converged, int32_t *iters_used, void *stream) {
+    mld::clear_error();
+    if (!g) return mld::fail(MLD_EINVAL, "decode_noalloc: null graph");
+    if (msg_dtype != MLD_MSG_F32 && msg_dtype != MLD_MSG_F16)
+        return mld::fail(MLD_EINVAL, "decode_noalloc: unknown msg_dtype");
+    if (flags & ~(MLD_EARLY_TERM | MLD_DEVICE_PTRS)) return mld::fail(MLD_EINVAL, "decode_noalloc: unknown flag");
+    if (batch < 0 || max_iters < 0) return mld::fail(MLD_EINVAL, "decode_noalloc: negative batch or max_iters");
+    if (batch == 0) return MLD_OK;
+    const mld::HostGraph &h = g->h;
+    if ((h.n_vn > 0 && (!llr || !bits_out)) || (h.n_cn > 0 && !syndrome) || !converged || !iters_used)
+        return mld::fail(MLD_EINVAL, "decode_noalloc: null data pointer");
+    int s = check_device(g->device);
+    if (s != MLD_OK) return s;
+    const int W = msg_dtype == MLD_MSG_F16 ? 64 : 32;
+    const size_t msz = msg_dtype == MLD_MSG_F16 ? 2 : 4;
+    const int slabs = (batch + W - 1) / W;
+    const NoallocLayout L = noalloc_layout(h, W, msz, slabs);
+    if (L.total > static_cast<size_t>(MLD_NOALLOC_SCRATCH_BYTES))
+        return mld::fail(MLD_EINVAL, "decode_noalloc: this graph and batch need " + std::to_string(L.total) +
+                                         " bytes of scratch; the static array holds " +
+                                         std::to_string(static_cast<size_t>(MLD_NOALLOC_SCRATCH_BYTES)));
+    void *base_v = nullptr;
+    s = noalloc_base(g->device, &base_v);
+    if (s != MLD_OK) return s;
+    unsigned char *base = static_cast<unsigned char *>(base_v);
+    // a decoder view onto the scratch array: nothing here is freed
+    mld_decoder d;
+    d.g = g;
+    d.device = g->device;
+    d.msg = msg_dtype;
+    d.W = W;
+    d.max_batch = batch;
+    d.max_slabs = slabs;
+    d.lmax = 25.f;
+    d.amin = static_cast<float>(phi_host(25.0));
+    d.r = base + L.r;
+    d.Lv = reinterpret_cast<float *>(base + L.Lv);
+    d.lch = reinterpret_cast<float *>(base + L.lch);
+    d.lch1 = reinterpret_cast<float *>(base + L.lch1);
+    d.post1 = reinterpret_cast<float *>(base + L.post1);
+    d.hb_core = base + L.hb_core;
+    d.hb1 = base + L.hb1;
+    d.sbits = base + L.sbits;
+    d.done = reinterpret_cast<uint32_t *>(base + L.done);
+    d.fail = reinterpret_cast<uint32_t *>(base + L.fail);
+    d.iters = reinterpret_cast<int32_t *>(base + L.iters);
+    d.conv = base + L.conv;
+    const bool et = (flags & MLD_EARLY_TERM) != 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return msg_dtype == MLD_MSG_F16
+               ? dispatch_w<__half>(&d, llr, nullptr, syndrome, batch, max_iters, et, bits_out, post_out,
+                                    converged, iters_used, st, true)
+               : dispatch_w<float>(&d, llr, nullptr, syndrome, batch, max_iters, et, bits_out, post_out,
+                                   converged, iters_used, st, true);
+}
