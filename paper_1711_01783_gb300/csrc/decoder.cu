@@ -93,27 +93,11 @@ __device__ __forceinline__ float phi_f(float x) {
     return sel_lt(x, MLD_PHI_X0, phi_small(x), phi_large(x));
 }
 
-// phi of four values.  A piece is evaluated only if some lane of the warp
-// needs it (one MUFU op per value instead of two when the warp agrees); the
-// result equals phi_f element by element.  Must be called by all 32 lanes.
+// phi of four values.  Both pieces are evaluated for every value and the
+// right one selected without branches, so the compiler can interleave the
+// four dependency chains and those of neighbouring terms.
 __device__ __forceinline__ float4 phi4(float4 x) {
-    const float mn = fminf(fminf(x.x, x.y), fminf(x.z, x.w));
-    const float mx = fmaxf(fmaxf(x.x, x.y), fmaxf(x.z, x.w));
-    const bool need_s = __any_sync(0xFFFFFFFFu, mn < MLD_PHI_X0);
-    const bool need_l = __any_sync(0xFFFFFFFFu, mx >= MLD_PHI_X0);
-    float4 r;
-    if (need_l) {
-        r = make_float4(phi_large(x.x), phi_large(x.y), phi_large(x.z), phi_large(x.w));
-        if (need_s) {
-            r.x = sel_lt(x.x, MLD_PHI_X0, phi_small(x.x), r.x);
-            r.y = sel_lt(x.y, MLD_PHI_X0, phi_small(x.y), r.y);
-            r.z = sel_lt(x.z, MLD_PHI_X0, phi_small(x.z), r.z);
-            r.w = sel_lt(x.w, MLD_PHI_X0, phi_small(x.w), r.w);
-        }
-    } else {
-        r = make_float4(phi_small(x.x), phi_small(x.y), phi_small(x.z), phi_small(x.w));
-    }
-    return r;
+    return make_float4(phi_f(x.x), phi_f(x.y), phi_f(x.z), phi_f(x.w));
 }
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
@@ -188,6 +172,7 @@ struct CnArgs {
     void *r;               // [slab][e_core][W] messages
     const float *Lv;       // [slab][n_core][W] core posteriors of the previous iteration
     const float *lch1;     // [slab][n_deg1][W] degree-1 channel LLRs
+    const float *phi1;     // [slab][n_deg1][W] phi(|L_ch|) with the sign of L_ch (constant)
     float *post1;          // [slab][n_deg1][W] degree-1 posteriors (final / ET pass)
     uint8_t *hb1;          // [slab][n_deg1][W/8] degree-1 hard decisions
     const uint8_t *sbits;  // [slab][n_cn][W/8] syndrome bits
@@ -231,8 +216,7 @@ __device__ __forceinline__ void store_r(const CnArgs &a, MsgT *rp, float4 rv, ui
     Msg<MsgT>::store(rp, rv);
 }
 
-using mld::ClassTable;
-using mld::kMaxEntries;
+using mld::ClassLaunch;
 
 __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
 __device__ __forceinline__ float bitsf(uint32_t x) { return __uint_as_float(x); }
@@ -242,19 +226,18 @@ constexpr uint32_t kSign = 0x80000000u;
 // of the warp runs this (threads past the class end work on its last check
 // and store nothing), so phi4 may vote.
 template <typename MsgT, int W, int D>
-__device__ __forceinline__ void check_regular(const CnArgs &a, const ClassTable &ct, int k,
-                                              int64_t lt, int slab) {
+__device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch &cl, int64_t lt, int slab) {
     constexpr int TPC = W / kK;
     constexpr int NB = W / 8;
-    const int32_t count = ct.count[k];
+    const int32_t count = cl.count;
     int32_t j = static_cast<int32_t>(lt / TPC);
     const bool valid = j < count;
     if (!valid) j = count - 1;
     const int lane0 = static_cast<int>(lt % TPC) * kK;
-    const int dc = ct.dc[k];
-    const int32_t c = ct.c0[k] + j;
-    const int32_t e0 = ct.e0[k] + j * dc;
-    const int32_t s0 = ct.s0[k] + j * (D - dc);
+    const int dc = cl.dc;
+    const int32_t c = cl.c0 + j;
+    const int32_t e0 = cl.e0 + j * dc;
+    const int32_t s0 = cl.s0 + j * (D - dc);
     const float lmax = a.lmax, amin = a.amin;
 
     const uint32_t sb =
@@ -263,36 +246,41 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassTable 
     const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
     MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
     const float *lvb = a.Lv + static_cast<size_t>(slab) * a.n_core * W + lane0;
-    const float *l1b = a.lch1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
+    const float *p1b = a.phi1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
 
     int32_t vidx[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) vidx[i] = (i < dc) ? __ldg(a.col + e0 + i) : 0;
 
     // pass 1: f = phi(|q|) carrying the sign of q in its sign bit; the top
-    // bit of par accumulates the sign parity (syndrome bit included)
+    // bit of par accumulates the sign parity (syndrome bit included).  For a
+    // degree-1 VN q is its channel LLR, whose f was formed once on entry.
     float f[D][kK];
     uint32_t par[kK];
 #pragma unroll
     for (int kk = 0; kk < kK; ++kk) par[kk] = ((sb >> kk) & 1u) << 31;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-        float4 q;
         if (i < dc) {
             const float4 lv = ldf4(lvb + static_cast<size_t>(vidx[i]) * W);
             const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
-            q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
-        } else {
-            q = ldf4(l1b + static_cast<size_t>(s0 + i - dc) * W);
-        }
-        const float4 m = make_float4(clampf(fabsf(q.x), amin, lmax), clampf(fabsf(q.y), amin, lmax),
-                                     clampf(fabsf(q.z), amin, lmax), clampf(fabsf(q.w), amin, lmax));
-        const float4 ph = phi4(m);
+            const float4 q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
+            const float4 m = make_float4(clampf(fabsf(q.x), amin, lmax), clampf(fabsf(q.y), amin, lmax),
+                                         clampf(fabsf(q.z), amin, lmax), clampf(fabsf(q.w), amin, lmax));
+            const float4 ph = phi4(m);
 #pragma unroll
-        for (int kk = 0; kk < kK; ++kk) {
-            const uint32_t qb = fbits(f4get(q, kk));
-            f[i][kk] = bitsf(fbits(f4get(ph, kk)) | (qb & kSign));
-            par[kk] ^= qb;
+            for (int kk = 0; kk < kK; ++kk) {
+                const uint32_t qb = fbits(f4get(q, kk));
+                f[i][kk] = bitsf(fbits(f4get(ph, kk)) | (qb & kSign));
+                par[kk] ^= qb;
+            }
+        } else {
+            const float4 p = ldf4(p1b + static_cast<size_t>(s0 + i - dc) * W);
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) {
+                f[i][kk] = f4get(p, kk);
+                par[kk] ^= fbits(f[i][kk]);
+            }
         }
     }
     // exclusive prefix sums of |f|
@@ -340,14 +328,13 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassTable 
 // total minus own term.  Threads of a check pair stay together; nothing here
 // needs the whole warp.
 template <typename MsgT, int W>
-__device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassTable &ct, int k,
-                                                int64_t lt, int slab) {
+__device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaunch &cl, int64_t lt, int slab) {
     constexpr int TPC = W / kK;
     constexpr int NB = W / 8;
     const int32_t j = static_cast<int32_t>(lt / TPC);
-    if (j >= ct.count[k]) return;
+    if (j >= cl.count) return;
     const int lane0 = static_cast<int>(lt % TPC) * kK;
-    const int32_t c = ct.c0[k] + j;
+    const int32_t c = cl.c0 + j;
     const int32_t e0 = a.cptr[c], e1 = a.cptr[c + 1];
     const int32_t s0 = a.dptr[c], s1 = a.dptr[c + 1];
     const int nce = e1 - e0;
@@ -366,7 +353,7 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassTabl
             const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
             return make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
         }
-        return ldf4(l1b + static_cast<size_t>(s0 + i - nce) * W);
+        return ldf4(l1b + static_cast<size_t>(s0 + i - nce) * W);  // q = L_ch
     };
     float S[kK] = {0.f, 0.f, 0.f, 0.f};
     uint32_t par[kK];
@@ -400,25 +387,35 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassTabl
     }
 }
 
-// DMAX: the largest register-held degree in the table (4, 6 or 8); smaller
-// tables compile to smaller register arrays and higher occupancy.
-template <typename MsgT, int W, int DMAX>
-__global__ void __launch_bounds__(kBlock, (DMAX <= 6 ? 4 : 2)) k_check_update(CnArgs a, ClassTable ct) {
+// One check class per launch, its degree D a compile-time constant: the
+// register arrays are sized exactly and only this class's code is hot.
+template <typename MsgT, int W, int D>
+__global__ void __launch_bounds__(kBlock, (D <= 6 ? 4 : 3)) k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
-    int k = 0;
-    while (k + 1 < ct.n && static_cast<int32_t>(blockIdx.x) >= ct.block0[k + 1]) ++k;
-    const int64_t lt = static_cast<int64_t>(blockIdx.x - ct.block0[k]) * blockDim.x + threadIdx.x;
-    switch (ct.deg[k]) {
-        case 1: check_regular<MsgT, W, 1>(a, ct, k, lt, slab); break;
-        case 2: check_regular<MsgT, W, 2>(a, ct, k, lt, slab); break;
-        case 3: check_regular<MsgT, W, 3>(a, ct, k, lt, slab); break;
-        case 4: check_regular<MsgT, W, 4>(a, ct, k, lt, slab); break;
-        case 5: if constexpr (DMAX >= 5) check_regular<MsgT, W, 5>(a, ct, k, lt, slab); break;
-        case 6: if constexpr (DMAX >= 6) check_regular<MsgT, W, 6>(a, ct, k, lt, slab); break;
-        case 7: if constexpr (DMAX >= 7) check_regular<MsgT, W, 7>(a, ct, k, lt, slab); break;
-        case 8: if constexpr (DMAX >= 8) check_regular<MsgT, W, 8>(a, ct, k, lt, slab); break;
-        default: check_irregular<MsgT, W>(a, ct, k, lt, slab); break;
+    check_regular<MsgT, W, D>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, slab);
+}
+
+template <typename MsgT, int W>
+__global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, ClassLaunch cl) {
+    const int slab = blockIdx.y;
+    if (a.et && slab_all_done<W>(a.done, slab)) return;
+    check_irregular<MsgT, W>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, slab);
+}
+
+template <typename MsgT, int W>
+void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st) {
+    const dim3 grid(cl.blocks, slabs);
+    switch (cl.deg) {
+        case 1: k_check_update<MsgT, W, 1><<<grid, kBlock, 0, st>>>(ca, cl); break;
+        case 2: k_check_update<MsgT, W, 2><<<grid, kBlock, 0, st>>>(ca, cl); break;
+        case 3: k_check_update<MsgT, W, 3><<<grid, kBlock, 0, st>>>(ca, cl); break;
+        case 4: k_check_update<MsgT, W, 4><<<grid, kBlock, 0, st>>>(ca, cl); break;
+        case 5: k_check_update<MsgT, W, 5><<<grid, kBlock, 0, st>>>(ca, cl); break;
+        case 6: k_check_update<MsgT, W, 6><<<grid, kBlock, 0, st>>>(ca, cl); break;
+        case 7: k_check_update<MsgT, W, 7><<<grid, kBlock, 0, st>>>(ca, cl); break;
+        case 8: k_check_update<MsgT, W, 8><<<grid, kBlock, 0, st>>>(ca, cl); break;
+        default: k_check_update_irregular<MsgT, W><<<grid, kBlock, 0, st>>>(ca, cl); break;
     }
 }
 
@@ -545,8 +542,8 @@ struct InArgs {
     const float *sigma;   // [B] or null (input is already an LLR)
     const int32_t *unit;
     int32_t n_vn, n_core, n_deg1, batch;
-    float lmax;
-    float *lch, *Lv, *lch1, *post1;
+    float lmax, amin;
+    float *lch, *Lv, *lch1, *post1, *phi1;
 };
 
 template <int W>
@@ -584,6 +581,10 @@ __global__ void __launch_bounds__(kBlock) k_interleave_in(InArgs a) {
             const size_t o = (static_cast<size_t>(slab) * a.n_deg1 + (u - a.n_core)) * W + w;
             a.lch1[o] = v;
             a.post1[o] = v;
+            // the degree-1 VN's message never changes: its phi term, with the
+            // sign of the LLR, is formed once here for every check update
+            const float f = phi_f(clampf(fabsf(v), a.amin, a.lmax));
+            a.phi1[o] = bitsf(fbits(f) | (fbits(v) & kSign));
         }
     }
 }
@@ -724,36 +725,25 @@ int grid_x(int64_t threads) {
 
 }  // namespace
 
-// Launch tables of the check update for each slab width: one entry per check
-// class, entries grouped kMaxEntries to a launch.
+// Check-update launches for each slab width: one per check class that has
+// edges, with its grid size.
 void build_class_tables(mld_graph *g) {
     const int widths[4] = {8, 16, 32, 64};
     for (int wi = 0; wi < 4; ++wi) {
         const int tpc = widths[wi] / kK;
-        std::vector<ClassTable> &tables = g->tables[wi];
-        tables.clear();
-        ClassTable t{};
+        std::vector<ClassLaunch> &out = g->launches[wi];
+        out.clear();
         for (const mld::CheckClass &cl : g->h.classes) {
             if (cl.dc == 0 && cl.dd == 0) continue;  // checks without edges: nothing to send
-            if (t.n == kMaxEntries) {
-                tables.push_back(t);
-                t = ClassTable{};
-            }
-            const int i = t.n++;
-            t.c0[i] = cl.c0;
-            t.count[i] = cl.count;
-            t.dc[i] = cl.dc;
-            t.deg[i] = cl.dc < 0 ? -1 : cl.dc + cl.dd;
-            t.e0[i] = cl.e0;
-            t.s0[i] = cl.s0;
-            t.block0[i + 1] = t.block0[i] + grid_x(static_cast<int64_t>(cl.count) * tpc);
-        }
-        if (t.n > 0) tables.push_back(t);
-        g->table_dmax[wi].clear();
-        for (const ClassTable &tt : tables) {
-            int m = 0;
-            for (int i = 0; i < tt.n; ++i) m = std::max(m, tt.deg[i]);
-            g->table_dmax[wi].push_back(m);
+            ClassLaunch l;
+            l.c0 = cl.c0;
+            l.count = cl.count;
+            l.dc = cl.dc;
+            l.deg = cl.dc < 0 ? -1 : cl.dc + cl.dd;
+            l.e0 = cl.e0;
+            l.s0 = cl.s0;
+            l.blocks = grid_x(static_cast<int64_t>(cl.count) * tpc);
+            out.push_back(l);
         }
     }
 }
@@ -770,7 +760,7 @@ struct mld_decoder {
     int max_slabs = 0;
     float lmax = 25.f, amin = 0.f;
     void *r = nullptr;
-    float *Lv = nullptr, *lch = nullptr, *lch1 = nullptr, *post1 = nullptr;
+    float *Lv = nullptr, *lch = nullptr, *lch1 = nullptr, *post1 = nullptr, *phi1 = nullptr;
     uint8_t *hb_core = nullptr, *hb1 = nullptr, *sbits = nullptr;
     uint32_t *done = nullptr, *fail = nullptr;
     int32_t *iters = nullptr;
@@ -792,7 +782,7 @@ void decoder_free(mld_decoder *d) {
     if (!d) return;
     if (d->r) cudaFree(d->r);
     d->r = nullptr;
-    dfree(d->Lv); dfree(d->lch); dfree(d->lch1); dfree(d->post1);
+    dfree(d->Lv); dfree(d->lch); dfree(d->lch1); dfree(d->post1); dfree(d->phi1);
     dfree(d->hb_core); dfree(d->hb1); dfree(d->sbits);
     dfree(d->done); dfree(d->fail); dfree(d->iters); dfree(d->conv); dfree(d->status);
     dfree(d->in_stage); dfree(d->sigma_stage); dfree(d->post_stage);
@@ -858,8 +848,8 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     if (rbytes) MLD_CUDA(cudaMemsetAsync(d->r, 0, rbytes, st));
     MLD_CUDA(cudaMemsetAsync(d->done, 0, sizeof(uint32_t) * slabs * DW, st));
 
-    InArgs ia{in, sigma, g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->lmax,
-              d->lch, d->Lv, d->lch1, d->post1};
+    InArgs ia{in, sigma, g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->lmax, d->amin,
+              d->lch, d->Lv, d->lch1, d->post1, d->phi1};
     if (h.n_vn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_interleave_in", [&] {
             k_interleave_in<W><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(ia);
@@ -875,15 +865,14 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     }
 
     CnArgs ca{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, h.e_core,
-              d->r, d->Lv, d->lch1, d->post1, d->hb1, d->sbits, d->done,
+              d->r, d->Lv, d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done,
               d->lmax, d->amin, 0, et ? 1 : 0};
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
                d->fail, d->done, et ? 1 : 0};
-    // launch tables for the check classes (built with the graph)
+    // check-update launches, one per check class (built with the graph)
     const int wi = W == 8 ? 0 : (W == 16 ? 1 : (W == 32 ? 2 : 3));
-    const std::vector<ClassTable> &tables = g->tables[wi];
-    const std::vector<int> &table_dmax = g->table_dmax[wi];
+    const std::vector<ClassLaunch> &launches = g->launches[wi];
     const dim3 vn_grid(grid_x(static_cast<int64_t>(h.n_core) * TPC), slabs);
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, d->device);
@@ -928,17 +917,9 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     for (int32_t l = 1; l <= iters; ++l) {
         const bool last = (l == iters);
         ca.final_pass = (last || et) ? 1 : 0;
-        for (size_t ti = 0; ti < tables.size(); ++ti) {
-            const ClassTable &t = tables[ti];
-            const dim3 grid(t.block0[t.n], slabs);
-            int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
-                if (table_dmax[ti] <= 4)
-                    k_check_update<MsgT, W, 4><<<grid, kBlock, 0, st>>>(ca, t);
-                else if (table_dmax[ti] <= 6)
-                    k_check_update<MsgT, W, 6><<<grid, kBlock, 0, st>>>(ca, t);
-                else
-                    k_check_update<MsgT, W, 8><<<grid, kBlock, 0, st>>>(ca, t);
-            });
+        for (const ClassLaunch &cl : launches) {
+            int s = timed_launch(d, kClsCheck, st, "k_check_update",
+                                 [&] { launch_check_class<MsgT, W>(ca, cl, slabs, st); });
             if (s != MLD_OK) return s;
         }
         va.want_bits = (last || et) ? 1 : 0;
@@ -1138,6 +1119,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     if (s == MLD_OK) s = dalloc(&d->lch, S * h.n_core * W);
     if (s == MLD_OK) s = dalloc(&d->lch1, S * h.n_deg1 * W);
     if (s == MLD_OK) s = dalloc(&d->post1, S * h.n_deg1 * W);
+    if (s == MLD_OK) s = dalloc(&d->phi1, S * h.n_deg1 * W);
     if (s == MLD_OK) s = dalloc(&d->hb_core, S * h.n_core * NB);
     if (s == MLD_OK) s = dalloc(&d->hb1, S * h.n_deg1 * NB);
     if (s == MLD_OK) s = dalloc(&d->sbits, S * h.n_cn * NB);
@@ -1267,7 +1249,7 @@ int noalloc_base(int dev, void **out) {
 
 // Offsets of the working buffers inside the scratch array (256-byte aligned).
 struct NoallocLayout {
-    size_t r, Lv, lch, lch1, post1, hb_core, hb1, sbits, done, fail, iters, conv, total;
+    size_t r, Lv, lch, lch1, post1, phi1, hb_core, hb1, sbits, done, fail, iters, conv, total;
 };
 
 NoallocLayout noalloc_layout(const mld::HostGraph &h, int W, size_t msz, int slabs) {
@@ -1285,6 +1267,7 @@ NoallocLayout noalloc_layout(const mld::HostGraph &h, int W, size_t msz, int sla
     L.lch = take(S * h.n_core * W * sizeof(float));
     L.lch1 = take(S * h.n_deg1 * W * sizeof(float));
     L.post1 = take(S * h.n_deg1 * W * sizeof(float));
+    L.phi1 = take(S * h.n_deg1 * W * sizeof(float));
     L.hb_core = take(S * h.n_core * NB);
     L.hb1 = take(S * h.n_deg1 * NB);
     L.sbits = take(S * h.n_cn * NB);
@@ -1341,6 +1324,7 @@ extern "C" int mld_decode_noalloc(const mld_graph *g, int32_t msg_dtype, const f
     d.lch = reinterpret_cast<float *>(base + L.lch);
     d.lch1 = reinterpret_cast<float *>(base + L.lch1);
     d.post1 = reinterpret_cast<float *>(base + L.post1);
+    d.phi1 = reinterpret_cast<float *>(base + L.phi1);
     d.hb_core = base + L.hb_core;
     d.hb1 = base + L.hb1;
     d.sbits = base + L.sbits;

@@ -54,15 +54,11 @@ struct HostGraph {
     std::vector<uint8_t> etype_core, etype_deg1;
 };
 
-// Launch table of the check update: one entry per check class.  Entry k
-// covers blocks block0[k] .. block0[k+1]-1 of the grid; `deg` = dc + dd for a
-// class handled in registers, or -1 for checks read through cptr/dptr.
-constexpr int kMaxEntries = 16;
-struct ClassTable {
-    int32_t n;
-    int32_t block0[kMaxEntries + 1];
-    int32_t c0[kMaxEntries], count[kMaxEntries], dc[kMaxEntries], deg[kMaxEntries];
-    int32_t e0[kMaxEntries], s0[kMaxEntries];
+// One launch of the check update: a check class with its grid size for one
+// slab width.  `deg` = dc + dd for a class held in registers (1..kMaxRegDeg),
+// or -1 for checks read through cptr/dptr.
+struct ClassLaunch {
+    int32_t c0, count, dc, deg, e0, s0, blocks;
 };
 
 int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
@@ -78,7 +74,6 @@ struct mld_graph {
     int32_t *cptr = nullptr, *col = nullptr, *dptr = nullptr;
     int32_t *vptr = nullptr, *vedge = nullptr, *unit = nullptr, *cint = nullptr;
     uint8_t *etype_core = nullptr, *etype_deg1 = nullptr;
-    // check-update launch tables per slab width (8, 16, 32, 64)
-    std::vector<mld::ClassTable> tables[4];
-    std::vector<int> table_dmax[4];
+    // check-update launches per slab width (8, 16, 32, 64)
+    std::vector<mld::ClassLaunch> launches[4];
 };
