@@ -60,6 +60,13 @@ def parse():
 
 DEFAULT_ITERS = {0.1: 100, 0.05: 150, 0.02: 200}
 
+# DRAM bytes (read + write) of one check-update pass per (codeword x bit),
+# from `ncu --set full` of the three check-class launches of one iteration
+# (rate 0.1, n = 3e5, 64 codewords, half messages: 395.86 MB); traffic
+# grows with n, so it is scaled by the units a full pass processes.  Valid
+# for the kernel of this commit only (see profiles/).
+CHECK_PASS_TRAFFIC_PER_CW_BIT = {(0.1, "f16"): 395.86e6 / (64 * 3e5)}
+
 
 def workload_config(a) -> dict:
     return {
@@ -314,8 +321,9 @@ def main():
     check_ms = kt["check_ms"] / max(1, passes)
     achieved = per_cw * a.batch / (check_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
+    tpb = CHECK_PASS_TRAFFIC_PER_CW_BIT.get((a.rate, a.msg))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": tpb * a.batch * a.n if tpb else None,
                 "kernel": "k_check_update (one pass = all check classes of one iteration)",
                 "peak_kind": peak_kind, "pass_ms": check_ms,
                 "algorithmic_bytes_per_pass": per_cw * a.batch,

@@ -236,8 +236,11 @@ int mld_decode_noalloc(const mld_graph *g, int32_t msg_dtype, const float *llr,
  * Evaluates on the device the float phi(x) = -ln tanh(x/2) that the check
  * update uses (the LLR-domain message map that the closing paragraph of the
  * Methods proposes to tabulate), for n inputs clamped to [phi(lmax), lmax]
- * with lmax = 25.  x and out are device float pointers [n]. */
-int mld_phi_eval(const float *x, float *out, int64_t n, void *stream);
+ * with lmax = 25.  msg_dtype selects the variant a decoder of that message
+ * storage type uses: MLD_MSG_F32 (relative error ~1e-7) or MLD_MSG_F16
+ * (a shorter fit, relative error ~4e-6, below half's 2^-11 rounding).
+ * x and out are device float pointers [n].  Errors: MLD_EINVAL, MLD_ECUDA. */
+int mld_phi_eval(int32_t msg_dtype, const float *x, float *out, int64_t n, void *stream);
 
 #ifdef __cplusplus
 }

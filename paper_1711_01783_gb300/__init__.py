@@ -80,7 +80,7 @@ def _load() -> ctypes.CDLL:
         "mld_decoder_timing_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "mld_decoder_timing_read": (ctypes.c_int, [P, ctypes.POINTER(Timing)]),
         "mld_decode_noalloc": (ctypes.c_int, [P, I32, P, P, I32, I32, U32, P, P, P, P, P]),
-        "mld_phi_eval": (ctypes.c_int, [P, P, I64, P]),
+        "mld_phi_eval": (ctypes.c_int, [I32, P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -302,12 +302,14 @@ def decode_noalloc(graph: Graph, llr, syndrome, iters: int, msg_dtype: str = "f3
     return out
 
 
-def phi(x, stream=None):
-    """Device phi(x) = -ln tanh(x/2) as used by the check update (float32 CUDA tensor)."""
+def phi(x, msg_dtype: str = "f32", stream=None):
+    """Device phi(x) = -ln tanh(x/2) as used by the check update of a decoder
+    with the given message storage type (float32 CUDA tensor in and out)."""
     torch = _torch()
     x = x.contiguous().to(torch.float32)
     out = torch.empty_like(x)
-    _check(lib().mld_phi_eval(_ptr(x), _ptr(out), x.numel(), _stream_handle(stream)))
+    dt = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
+    _check(lib().mld_phi_eval(dt, _ptr(x), _ptr(out), x.numel(), _stream_handle(stream)))
     return out
 
 

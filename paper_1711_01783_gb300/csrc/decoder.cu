@@ -60,23 +60,40 @@ __device__ __forceinline__ float mufu_ex2(float x) {
     return y;
 }
 
+// Piece below MLD_PHI_X0.  HALF selects the shorter fit used with half
+// message storage (error ~3e-6, far below half's 2^-11 rounding).
+template <bool HALF>
 __device__ __forceinline__ float phi_small(float x) {
     const float kLn2 = 0.693147180559945309f;
     const float t = x * x;
-    float ps = fmaf(MLD_PHI_S4, t, MLD_PHI_S3);
-    ps = fmaf(ps, t, MLD_PHI_S2);
-    ps = fmaf(ps, t, MLD_PHI_S1);
-    ps = fmaf(ps, t, MLD_PHI_S0);
+    float ps;
+    if constexpr (HALF) {
+        ps = fmaf(MLD_PHIH_S2, t, MLD_PHIH_S1);
+        ps = fmaf(ps, t, MLD_PHIH_S0);
+    } else {
+        ps = fmaf(MLD_PHI_S4, t, MLD_PHI_S3);
+        ps = fmaf(ps, t, MLD_PHI_S2);
+        ps = fmaf(ps, t, MLD_PHI_S1);
+        ps = fmaf(ps, t, MLD_PHI_S0);
+    }
     return fmaf(-t, ps, fmaf(-kLn2, mufu_lg2(x), kLn2));
 }
 
+// Piece at and above MLD_PHI_X0.
+template <bool HALF>
 __device__ __forceinline__ float phi_large(float x) {
     const float kLog2e = 1.442695040888963407f;
     const float e = mufu_ex2(-kLog2e * x);
     const float z = e * e;
-    float pl = fmaf(MLD_PHI_L3, z, MLD_PHI_L2);
-    pl = fmaf(pl, z, MLD_PHI_L1);
-    pl = fmaf(pl, z, MLD_PHI_L0);
+    float pl;
+    if constexpr (HALF) {
+        pl = fmaf(MLD_PHIH_L2, z, MLD_PHIH_L1);
+        pl = fmaf(pl, z, MLD_PHIH_L0);
+    } else {
+        pl = fmaf(MLD_PHI_L3, z, MLD_PHI_L2);
+        pl = fmaf(pl, z, MLD_PHI_L1);
+        pl = fmaf(pl, z, MLD_PHI_L0);
+    }
     return e * pl;
 }
 
@@ -88,17 +105,20 @@ __device__ __forceinline__ float sel_lt(float x, float th, float a, float b) {
     return r;
 }
 
-// phi of one value: both pieces, then the one for x.
+// phi of one value: both pieces are evaluated and the right one selected
+// without branches, so the compiler can interleave independent chains.
+template <bool HALF>
 __device__ __forceinline__ float phi_f(float x) {
-    return sel_lt(x, MLD_PHI_X0, phi_small(x), phi_large(x));
+    return sel_lt(x, MLD_PHI_X0, phi_small<HALF>(x), phi_large<HALF>(x));
 }
 
-// phi of four values.  Both pieces are evaluated for every value and the
-// right one selected without branches, so the compiler can interleave the
-// four dependency chains and those of neighbouring terms.
+template <bool HALF>
 __device__ __forceinline__ float4 phi4(float4 x) {
-    return make_float4(phi_f(x.x), phi_f(x.y), phi_f(x.z), phi_f(x.w));
+    return make_float4(phi_f<HALF>(x.x), phi_f<HALF>(x.y), phi_f<HALF>(x.z), phi_f<HALF>(x.w));
 }
+
+template <typename T> struct IsHalf { static constexpr bool value = false; };
+template <> struct IsHalf<__half> { static constexpr bool value = true; };
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
     return fminf(fmaxf(x, lo), hi);
@@ -222,19 +242,21 @@ __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); 
 __device__ __forceinline__ float bitsf(uint32_t x) { return __uint_as_float(x); }
 constexpr uint32_t kSign = 0x80000000u;
 
-// Checks of one class with D = dc + dd terms, all in registers.  Every thread
-// of the warp runs this (threads past the class end work on its last check
-// and store nothing), so phi4 may vote.
-template <typename MsgT, int W, int D>
+// Checks of one class: DC core edges and DD degree-1 VNs per check, all
+// terms in registers.  Threads past the class end work on its last check and
+// store nothing (so a whole shuffle pair stays active).
+template <typename MsgT, int W, int DC, int DD>
 __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch &cl, int64_t lt, int slab) {
     constexpr int TPC = W / kK;
     constexpr int NB = W / 8;
+    constexpr int D = DC + DD;
+    constexpr int dc = DC;
+    constexpr bool H = IsHalf<MsgT>::value;
     const int32_t count = cl.count;
     int32_t j = static_cast<int32_t>(lt / TPC);
     const bool valid = j < count;
     if (!valid) j = count - 1;
     const int lane0 = static_cast<int>(lt % TPC) * kK;
-    const int dc = cl.dc;
     const int32_t c = cl.c0 + j;
     const int32_t e0 = cl.e0 + j * dc;
     const int32_t s0 = cl.s0 + j * (D - dc);
@@ -267,7 +289,7 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             const float4 q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
             const float4 m = make_float4(clampf(fabsf(q.x), amin, lmax), clampf(fabsf(q.y), amin, lmax),
                                          clampf(fabsf(q.z), amin, lmax), clampf(fabsf(q.w), amin, lmax));
-            const float4 ph = phi4(m);
+            const float4 ph = phi4<H>(m);
 #pragma unroll
             for (int kk = 0; kk < kK; ++kk) {
                 const uint32_t qb = fbits(f4get(q, kk));
@@ -307,7 +329,7 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             float4 o = make_float4(fminf(pre[i][0] + suf[0], lmax), fminf(pre[i][1] + suf[1], lmax),
                                    fminf(pre[i][2] + suf[2], lmax), fminf(pre[i][3] + suf[3], lmax));
             if (D == 1) o = make_float4(amin, amin, amin, amin);
-            float4 m = phi4(o);
+            float4 m = phi4<H>(o);
             if (D <= 2) m = make_float4(fminf(m.x, lmax), fminf(m.y, lmax), fminf(m.z, lmax), fminf(m.w, lmax));
             float4 rv;
 #pragma unroll
@@ -331,6 +353,7 @@ template <typename MsgT, int W>
 __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaunch &cl, int64_t lt, int slab) {
     constexpr int TPC = W / kK;
     constexpr int NB = W / 8;
+    constexpr bool H = IsHalf<MsgT>::value;
     const int32_t j = static_cast<int32_t>(lt / TPC);
     if (j >= cl.count) return;
     const int lane0 = static_cast<int>(lt % TPC) * kK;
@@ -365,7 +388,7 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
         for (int kk = 0; kk < kK; ++kk) {
             const float qk = f4get(q, kk);
             par[kk] ^= fbits(qk);
-            S[kk] += phi_f(clampf(fabsf(qk), amin, lmax));
+            S[kk] += phi_f<H>(clampf(fabsf(qk), amin, lmax));
         }
     }
     for (int i = 0; i < deg; ++i) {
@@ -376,8 +399,8 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
 #pragma unroll
         for (int kk = 0; kk < kK; ++kk) {
             const float qk = f4get(q, kk);
-            const float fk = phi_f(clampf(fabsf(qk), amin, lmax));
-            const float mk = fminf(phi_f(clampf(S[kk] - fk, amin, lmax)), lmax);
+            const float fk = phi_f<H>(clampf(fabsf(qk), amin, lmax));
+            const float mk = fminf(phi_f<H>(clampf(S[kk] - fk, amin, lmax)), lmax);
             f4set(rv, kk, bitsf(fbits(mk) | ((par[kk] ^ fbits(qk)) & kSign)));
         }
         if (out_core)
@@ -387,13 +410,13 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
     }
 }
 
-// One check class per launch, its degree D a compile-time constant: the
+// One check class per launch, its shape (DC, DD) a compile-time constant: the
 // register arrays are sized exactly and only this class's code is hot.
-template <typename MsgT, int W, int D>
-__global__ void __launch_bounds__(kBlock, (D <= 6 ? 4 : 3)) k_check_update(CnArgs a, ClassLaunch cl) {
+template <typename MsgT, int W, int DC, int DD>
+__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 4 : 3)) k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
-    check_regular<MsgT, W, D>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, slab);
+    check_regular<MsgT, W, DC, DD>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, slab);
 }
 
 template <typename MsgT, int W>
@@ -403,20 +426,26 @@ __global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, Cla
     check_irregular<MsgT, W>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, slab);
 }
 
+// Classes with at most one degree-1 VN per check and at most kMaxRegDeg terms
+// run the register kernel for their shape; any other class (possible in
+// caller graphs, not in the MET ensembles) runs the streaming kernel.
 template <typename MsgT, int W>
 void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st) {
     const dim3 grid(cl.blocks, slabs);
-    switch (cl.deg) {
-        case 1: k_check_update<MsgT, W, 1><<<grid, kBlock, 0, st>>>(ca, cl); break;
-        case 2: k_check_update<MsgT, W, 2><<<grid, kBlock, 0, st>>>(ca, cl); break;
-        case 3: k_check_update<MsgT, W, 3><<<grid, kBlock, 0, st>>>(ca, cl); break;
-        case 4: k_check_update<MsgT, W, 4><<<grid, kBlock, 0, st>>>(ca, cl); break;
-        case 5: k_check_update<MsgT, W, 5><<<grid, kBlock, 0, st>>>(ca, cl); break;
-        case 6: k_check_update<MsgT, W, 6><<<grid, kBlock, 0, st>>>(ca, cl); break;
-        case 7: k_check_update<MsgT, W, 7><<<grid, kBlock, 0, st>>>(ca, cl); break;
-        case 8: k_check_update<MsgT, W, 8><<<grid, kBlock, 0, st>>>(ca, cl); break;
-        default: k_check_update_irregular<MsgT, W><<<grid, kBlock, 0, st>>>(ca, cl); break;
+    const int dd = cl.deg - cl.dc;
+#define MLD_CASE(DCV, DDV) \
+    case (DCV) * 2 + (DDV): k_check_update<MsgT, W, DCV, DDV><<<grid, kBlock, 0, st>>>(ca, cl); return;
+    if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
+        switch (cl.dc * 2 + dd) {
+            MLD_CASE(1, 0) MLD_CASE(2, 0) MLD_CASE(3, 0) MLD_CASE(4, 0)
+            MLD_CASE(5, 0) MLD_CASE(6, 0) MLD_CASE(7, 0) MLD_CASE(8, 0)
+            MLD_CASE(0, 1) MLD_CASE(1, 1) MLD_CASE(2, 1) MLD_CASE(3, 1)
+            MLD_CASE(4, 1) MLD_CASE(5, 1) MLD_CASE(6, 1) MLD_CASE(7, 1)
+            default: break;
+        }
     }
+#undef MLD_CASE
+    k_check_update_irregular<MsgT, W><<<grid, kBlock, 0, st>>>(ca, cl);
 }
 
 // ---------------------------------------------------------------------------
@@ -546,7 +575,7 @@ struct InArgs {
     float *lch, *Lv, *lch1, *post1, *phi1;
 };
 
-template <int W>
+template <int W, bool HALF>
 __global__ void __launch_bounds__(kBlock) k_interleave_in(InArgs a) {
     __shared__ float tile[W][33];
     const int slab = blockIdx.y;
@@ -583,7 +612,7 @@ __global__ void __launch_bounds__(kBlock) k_interleave_in(InArgs a) {
             a.post1[o] = v;
             // the degree-1 VN's message never changes: its phi term, with the
             // sign of the LLR, is formed once here for every check update
-            const float f = phi_f(clampf(fabsf(v), a.amin, a.lmax));
+            const float f = phi_f<HALF>(clampf(fabsf(v), a.amin, a.lmax));
             a.phi1[o] = bitsf(fbits(f) | (fbits(v) & kSign));
         }
     }
@@ -666,9 +695,10 @@ __global__ void __launch_bounds__(kBlock) k_deinterleave_out(OutArgs a) {
     }
 }
 
+template <bool HALF>
 __global__ void k_phi_eval(const float *x, float *out, int64_t n, float lmax, float amin) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = fminf(phi_f(clampf(x[i], amin, lmax)), lmax);
+    if (i < n) out[i] = fminf(phi_f<HALF>(clampf(x[i], amin, lmax)), lmax);
 }
 
 // ---------------------------------------------------------------------------
@@ -852,7 +882,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
               d->lch, d->Lv, d->lch1, d->post1, d->phi1};
     if (h.n_vn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_interleave_in", [&] {
-            k_interleave_in<W><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(ia);
+            k_interleave_in<W, IsHalf<MsgT>::value><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(ia);
         });
         if (s != MLD_OK) return s;
     }
@@ -1206,13 +1236,17 @@ int mld_decoder_timing_read(mld_decoder *d, mld_timing *out) {
     return status;
 }
 
-int mld_phi_eval(const float *x, float *out, int64_t n, void *stream) {
+int mld_phi_eval(int32_t msg_dtype, const float *x, float *out, int64_t n, void *stream) {
     mld::clear_error();
+    if (msg_dtype != MLD_MSG_F32 && msg_dtype != MLD_MSG_F16) return mld::fail(MLD_EINVAL, "phi_eval: msg_dtype");
     if (n < 0 || (n > 0 && (!x || !out))) return mld::fail(MLD_EINVAL, "phi_eval: bad arguments");
     if (n == 0) return MLD_OK;
     const float lmax = 25.f;
     const float amin = static_cast<float>(phi_host(25.0));
-    k_phi_eval<<<grid_x(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n, lmax, amin);
+    if (msg_dtype == MLD_MSG_F16)
+        k_phi_eval<true><<<grid_x(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n, lmax, amin);
+    else
+        k_phi_eval<false><<<grid_x(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n, lmax, amin);
     MLD_LAUNCHED("k_phi_eval");
     return MLD_OK;
 }

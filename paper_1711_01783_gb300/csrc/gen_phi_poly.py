@@ -20,45 +20,49 @@ import os
 import numpy as np
 
 X0 = 1.25
-DEG_SMALL = 5   # coefficients of Ps
-DEG_LARGE = 4   # coefficients of Pl
+# Two fits: "accurate" (used with float message storage; ~5e-8) and "half"
+# (used with half storage, whose rounding of 2^-11 dwarfs a ~3e-6 error).
+FITS = {"": (5, 4), "H": (3, 3)}   # prefix -> (coefficients of Ps, of Pl)
 
 
 def _cheb(lo, hi, k=6000):
     return lo + (hi - lo) * (np.cos(np.linspace(0, np.pi, k)) + 1) / 2
 
 
-def fit():
+def fit(deg_small, deg_large):
     t = _cheb(1e-10, X0 * X0)
     x = np.sqrt(t)
     h = np.log(np.tanh(x / 2) / (x / 2))
-    cs = np.polynomial.polynomial.polyfit(t, h / t, DEG_SMALL - 1)
+    cs = np.polynomial.polynomial.polyfit(t, h / t, deg_small - 1)
     err_s = np.max(np.abs(np.polynomial.polynomial.polyval(t, cs) * t - h))
     z = _cheb(1e-14, np.exp(-2 * X0))
     e = np.sqrt(z)
     pl = 2.0 * np.arctanh(e) / e
-    cl = np.polynomial.polynomial.polyfit(z, pl, DEG_LARGE - 1)
+    cl = np.polynomial.polynomial.polyfit(z, pl, deg_large - 1)
     err_l = np.max(np.abs(np.polynomial.polynomial.polyval(z, cl) / pl - 1))
     return cs, cl, err_s, err_l
 
 
 def main():
-    cs, cl, err_s, err_l = fit()
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "phi_poly.h")
     lines = [
         "// Generated by gen_phi_poly.py -- polynomial pieces of phi(x) = -ln tanh(x/2).",
-        f"// small branch x < {X0}: phi = ln2 - ln x - t*Ps(t), t = x^2; max |fit error| {err_s:.2e}",
-        f"// large branch: phi = e*Pl(e^2), e = exp(-x); max relative fit error {err_l:.2e}",
+        f"// small branch x < {X0}: phi = ln2 - ln x - t*Ps(t), t = x^2",
+        "// large branch: phi = e*Pl(e^2), e = exp(-x)",
         "#pragma once",
         f"#define MLD_PHI_X0 {X0:.9g}f",
     ]
-    for i, c in enumerate(cs):
-        lines.append(f"#define MLD_PHI_S{i} ({c:.9e}f)")
-    for i, c in enumerate(cl):
-        lines.append(f"#define MLD_PHI_L{i} ({c:.9e}f)")
+    for pre, (ds, dl) in FITS.items():
+        cs, cl, err_s, err_l = fit(ds, dl)
+        lines.append(f"// fit '{pre or 'accurate'}': max |small fit error| {err_s:.2e}, "
+                     f"max relative large fit error {err_l:.2e}")
+        for i, c in enumerate(cs):
+            lines.append(f"#define MLD_PHI{pre}_S{i} ({c:.9e}f)")
+        for i, c in enumerate(cl):
+            lines.append(f"#define MLD_PHI{pre}_L{i} ({c:.9e}f)")
+        print(pre, err_s, err_l)
     with open(out, "w") as f:
         f.write("\n".join(lines) + "\n")
-    print(out, err_s, err_l)
 
 
 if __name__ == "__main__":
