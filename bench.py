@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="fixed", choices=["fixed", "uneven"],
+                    help="fixed: one code, fixed iterations (the headline); uneven: 96 codewords over "
+                         "rates 0.1/0.05/0.02 and n in {2^16, 2^18, 10^6}, caps 100/150/200, early "
+                         "termination, one captured plan")
+    ap.add_argument("--tune-cache", default=None)
     return ap.parse_args()
 
 
@@ -198,8 +203,75 @@ def measured_peak_hbm() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+def run_uneven(a, world, rank, local):
+    """Uneven batch: every codeword draws its (rate, length); one plan (one
+    CUDA-graph launch) decodes all groups with per-codeword early termination
+    and each rate's iteration cap; slab widths chosen by the autotuner."""
+    import torch
+    import paper_1711_01783_gb300 as mld
+    from paper_1711_01783_gb300.tune import SlabWidthTuner
+    from synthetic import make_uneven_workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    groups = make_uneven_workload(a.batch, seed=3 + rank, beta=a.beta)
+    tuner = SlabWidthTuner(a.tune_cache)
+    jobs, widths = [], {}
+    for rate, n, wl in groups:
+        g = mld.Graph.from_edges(wl.graph)
+        B = wl.y.shape[0]
+        W = tuner.choose(g, B, a.msg)
+        widths[f"{rate}/{n}"] = (B, W)
+        jobs.append(dict(decoder=mld.Decoder(g, B, msg_dtype=a.msg, slab_width=W), y=torch.from_numpy(wl.y).to(dev),
+                         sigma=torch.from_numpy(wl.sigma).to(dev), syndrome=torch.from_numpy(wl.s).to(dev),
+                         max_iters=DEFAULT_ITERS[rate]))
+    plan = mld.Plan(jobs, early_term=True)
+    for _ in range(a.warmup):
+        plan.launch()
+    torch.cuda.synchronize()
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        outs = plan.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    bits = sum(wl.y.shape[0] * wl.y.shape[1] for _, _, wl in groups)
+    conv = sum(int(o["converged"].sum().item()) for o in outs)
+    its = [int(o["iters_used"].float().mean().item()) for o in outs]
+    line = {
+        "metric": "decoded Mbit/s, uneven batch (mixed rates and lengths, early termination)",
+        "value": bits / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MET ensembles, BIAWGN samples)",
+        "config": {"workload": f"{a.batch} codewords, (rate, n) uniform over {{0.1,0.05,0.02}} x "
+                               f"{{2^16,2^18,10^6}}, caps 100/150/200, early termination, beta={a.beta}",
+                   "msg_storage": a.msg, "groups (batch, slab width)": widths,
+                   "l2": "n=10^6 groups exceed L2"},
+        "gpu_launches": plan.launches * a.steps, "frames_converged": conv, "mean_iters": its,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.workload == "uneven":
+        if a.batch == 64:
+            a.batch = 96
+        if a.iters is None:
+            a.iters = 0
+        run_uneven(a, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+                   int(os.environ.get("LOCAL_RANK", "0")))
+        return
     if a.iters is None:
         a.iters = DEFAULT_ITERS.get(a.rate, 100)
     world = int(os.environ.get("WORLD_SIZE", "1"))

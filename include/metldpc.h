@@ -173,6 +173,56 @@ int mld_decode_y(mld_decoder *d, const float *y, const float *sigma,
  * (MLD_OK if none).  Synchronizes nothing; call after the stream is idle. */
 int mld_decode_status(mld_decoder *d);
 
+/* ---- uneven batches: several graphs in one launch --------------------------
+ * A job is a batch of codewords of one graph, decoded with its own decoder
+ * (which fixes the graph, message storage type, slab width and working
+ * memory) and its own iteration cap.  A plan turns a list of jobs into one
+ * schedule: in every iteration, one launch per kernel shape covers the work
+ * of all jobs that are still iterating (their caps differ), so codes of
+ * different rates and lengths share the GPU; the schedule is captured once
+ * into a CUDA graph and mld_plan_launch replays it with a single launch.
+ * This generalises the paper's multi-codeword decoding (Results, "High speed
+ * error correction with MET-LDPC codes"), which decodes one code at a time.
+ * Semantics per codeword are those of mld_decode_y / mld_decode with the
+ * job's max_iters; with MLD_EARLY_TERM each codeword stops at its first
+ * syndrome match (Methods, Step 5) and a slab whose codewords have all
+ * stopped is skipped.
+ *   decoder    : from mld_decoder_create; at most one job per decoder.
+ *   in         : device float [batch][n_vn]: observations y if sigma != NULL
+ *                (LLR = 2y/sigma^2 formed on the device), else channel LLRs.
+ *   sigma      : device float [batch] or NULL.
+ *   syndrome   : device uint8 [batch][n_cn].
+ *   batch      : 1 <= batch <= the decoder's max_batch.
+ *   max_iters  : >= 0.
+ *   bits_out, post_out (or NULL), converged, iters_used: device outputs as
+ *                for mld_decode.
+ * All pointers are device memory (MLD_DEVICE_PTRS is implied).  The plan
+ * records the pointers: they and the decoders must stay valid while the plan
+ * is used, and a plan's launches must not overlap with other work on the same
+ * decoders.  Errors: MLD_EINVAL (bad job, shared decoder, flag), MLD_ENOMEM,
+ * MLD_ECUDA. */
+typedef struct {
+    mld_decoder *decoder;
+    const float *in;
+    const float *sigma;
+    const uint8_t *syndrome;
+    int32_t batch;
+    int32_t max_iters;
+    uint8_t *bits_out;
+    float *post_out;
+    uint8_t *converged;
+    int32_t *iters_used;
+} mld_job;
+typedef struct mld_plan mld_plan;
+int mld_plan_create(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan **out);
+/* Enqueue the plan's CUDA graph on `stream` (one launch). */
+int mld_plan_launch(mld_plan *p, void *stream);
+/* Number of kernel launches inside the plan's graph. */
+int mld_plan_stats(const mld_plan *p, int64_t *launches);
+int mld_plan_destroy(mld_plan *p);
+/* Create a plan, launch it on `stream`, wait for the stream, destroy it. */
+int mld_decode_multi(const mld_job *jobs, int32_t n_jobs, uint32_t flags, void *stream);
+
 /* ---- kernel timing (measurement hook) -------------------------------------
  * With timing enabled, every later decode call on d records a pair of CUDA
  * events on its stream around each kernel it launches.  mld_decoder_timing_read

@@ -32,7 +32,8 @@ _STATUS = {MLD_EINVAL: "MLD_EINVAL", MLD_ENOMEM: "MLD_ENOMEM", MLD_ECUDA: "MLD_E
 EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destroy",
            "mld_graph_stats_get", "mld_decoder_create", "mld_decoder_destroy", "mld_decode",
            "mld_decode_y", "mld_decode_status", "mld_decoder_timing_enable",
-           "mld_decoder_timing_read", "mld_decode_noalloc", "mld_phi_eval")
+           "mld_decoder_timing_read", "mld_decode_noalloc", "mld_plan_create", "mld_plan_launch",
+           "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_phi_eval")
 
 
 class MldError(RuntimeError):
@@ -60,6 +61,13 @@ class Timing(ctypes.Structure):
                 ("syndrome_launches", ctypes.c_int64), ("layout_launches", ctypes.c_int64)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("decoder", ctypes.c_void_p), ("inp", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("syndrome", ctypes.c_void_p), ("batch", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("bits_out", ctypes.c_void_p), ("post_out", ctypes.c_void_p),
+                ("converged", ctypes.c_void_p), ("iters_used", ctypes.c_void_p)]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -80,6 +88,11 @@ def _load() -> ctypes.CDLL:
         "mld_decoder_timing_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "mld_decoder_timing_read": (ctypes.c_int, [P, ctypes.POINTER(Timing)]),
         "mld_decode_noalloc": (ctypes.c_int, [P, I32, P, P, I32, I32, U32, P, P, P, P, P]),
+        "mld_plan_create": (ctypes.c_int, [P, I32, U32, ctypes.POINTER(P)]),
+        "mld_plan_launch": (ctypes.c_int, [P, P]),
+        "mld_plan_stats": (ctypes.c_int, [P, ctypes.POINTER(I64)]),
+        "mld_plan_destroy": (ctypes.c_int, [P]),
+        "mld_decode_multi": (ctypes.c_int, [P, I32, U32, P]),
         "mld_phi_eval": (ctypes.c_int, [I32, P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
@@ -136,11 +149,16 @@ class Graph:
     """Tanner graph uploaded to the current CUDA device (mld_graph_create)."""
 
     def __init__(self, edge_vn, edge_cn, n_vn: int, n_cn: int, edge_type=None):
+        import hashlib
         ev = np.ascontiguousarray(edge_vn, dtype=np.int32)
         ec = np.ascontiguousarray(edge_cn, dtype=np.int32)
         et = None if edge_type is None else np.ascontiguousarray(edge_type, dtype=np.uint8)
         if ev.shape != ec.shape or (et is not None and et.shape != ev.shape):
             raise ValueError("edge arrays differ in length")
+        hsh = hashlib.sha1(np.array([n_vn, n_cn, ev.shape[0]], np.int64).tobytes())
+        hsh.update(ev.tobytes())
+        hsh.update(ec.tobytes())
+        self.signature = hsh.hexdigest()[:16]
         h = ctypes.c_void_p()
         _check(lib().mld_graph_create(_ptr(ev), _ptr(ec), _ptr(et), ev.shape[0], int(n_vn), int(n_cn),
                                      ctypes.byref(h)))
@@ -277,6 +295,62 @@ class Decoder:
         return {f: getattr(t, f) for f, _ in Timing._fields_}
 
 
+class Plan:
+    """Several jobs (graph + batch + iteration cap) decoded by one captured
+    CUDA graph (mld_plan_create / mld_plan_launch).
+
+    ``jobs`` is a list of dicts with keys ``decoder`` (Decoder), ``y`` (CUDA
+    float32 [B, n]; observations if ``sigma`` is given, else LLRs), ``sigma``
+    (CUDA float32 [B] or None), ``syndrome`` (CUDA uint8 [B, m]) and
+    ``max_iters``.  Outputs are allocated here and returned by ``outputs``.
+    """
+
+    def __init__(self, jobs, early_term: bool = False, want_post: bool = False):
+        torch = _torch()
+        self._keep = []
+        self.outputs = []
+        arr = (Job * max(1, len(jobs)))()
+        for i, jb in enumerate(jobs):
+            dec = jb["decoder"]
+            y = jb["y"].contiguous()
+            syn = jb["syndrome"].contiguous().to(torch.uint8)
+            sig = jb.get("sigma")
+            sig = sig.contiguous().to(torch.float32) if sig is not None else None
+            B, n = int(y.shape[0]), dec.graph.n_vn
+            o = dict(bits=torch.empty((B, n), dtype=torch.uint8, device=y.device),
+                     post=torch.empty((B, n), dtype=torch.float32, device=y.device) if want_post else None,
+                     converged=torch.empty(B, dtype=torch.uint8, device=y.device),
+                     iters_used=torch.empty(B, dtype=torch.int32, device=y.device))
+            self._keep += [dec, y, syn, sig]
+            self.outputs.append(o)
+            arr[i] = Job(dec.handle.value, y.data_ptr(), sig.data_ptr() if sig is not None else None,
+                         syn.data_ptr(), B, int(jb["max_iters"]), o["bits"].data_ptr(),
+                         o["post"].data_ptr() if o["post"] is not None else None,
+                         o["converged"].data_ptr(), o["iters_used"].data_ptr())
+        h = ctypes.c_void_p()
+        flags = (MLD_EARLY_TERM if early_term else 0) | MLD_DEVICE_PTRS
+        _check(lib().mld_plan_create(ctypes.cast(arr, ctypes.c_void_p), len(jobs), flags, ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_int64()
+        _check(lib().mld_plan_stats(h, ctypes.byref(n)))
+        self.launches = int(n.value)
+
+    def launch(self, stream=None):
+        _check(lib().mld_plan_launch(self._h, _stream_handle(stream)))
+        return self.outputs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mld_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -313,5 +387,5 @@ def phi(x, msg_dtype: str = "f32", stream=None):
     return out
 
 
-__all__ = ["Graph", "Decoder", "phi", "decode_noalloc", "version", "lib", "MldError", "EXPORTS",
+__all__ = ["Graph", "Decoder", "Plan", "phi", "decode_noalloc", "version", "lib", "MldError", "EXPORTS",
            "LIB_PATH", "NOALLOC_SCRATCH_BYTES"]

@@ -16,10 +16,10 @@ the workload the decoder is given.
 from .ensemble import MetGraph, met_ensemble, RATE_PRESETS, preset_graph
 from .channel import (biawgn_capacity, awgn_capacity, sigma_for_beta,
                       random_bits, bob_syndrome, biawgn_observe, Workload,
-                      make_workload)
+                      make_workload, make_uneven_workload)
 
 __all__ = [
     "MetGraph", "met_ensemble", "RATE_PRESETS", "preset_graph",
     "biawgn_capacity", "awgn_capacity", "sigma_for_beta", "random_bits",
-    "bob_syndrome", "biawgn_observe", "Workload", "make_workload",
+    "bob_syndrome", "biawgn_observe", "Workload", "make_workload", "make_uneven_workload",
 ]

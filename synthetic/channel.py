@@ -114,3 +114,24 @@ def make_workload(rate: float, n: int, batch: int, graph_seed: int,
     return Workload(graph=g, x=x, s=s, y=y,
                     sigma=np.full(batch, sig, dtype=np.float32),
                     rate=rate, beta=beta, seed=data_seed)
+
+
+def make_uneven_workload(total: int, rates=(0.1, 0.05, 0.02), lengths=(2 ** 16, 2 ** 18, 10 ** 6),
+                         seed: int = 3, beta: float = 0.90, graph_seed: int = 40):
+    """Codewords whose (rate, length) pair is drawn uniformly per codeword.
+
+    Returns a list of groups ``(rate, n, Workload)``, one per pair that was
+    drawn, each with its own graph (seed graph_seed + pair index) and the
+    sigma of its rate at efficiency ``beta``.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(total)]))
+    pairs = [(r, n) for r in rates for n in lengths]
+    draws = rng.integers(0, len(pairs), size=total)
+    groups = []
+    for k, (r, n) in enumerate(pairs):
+        b = int((draws == k).sum())
+        if b == 0:
+            continue
+        wl = make_workload(r, n, b, graph_seed + k, 5000 + 100 * k, beta=beta)
+        groups.append((r, n, wl))
+    return groups
