@@ -8,6 +8,10 @@ The arithmetic lives in ``oracle.c`` (plain C, FP64, one codeword per
 thread); see that file's header for the paper passages it follows and the
 readings it takes.  This module compiles it with gcc and wraps it with ctypes.
 
+Weighted BP (``wbp``): forward plus a hand-written reverse-mode gradient,
+pinned by central finite differences of its own FP64 loss and by the
+all-weights-one case equalling plain BP.
+
 Parity status: plain BP is pinned by brute-force bitwise MAP on cycle-free
 graphs, the single-check and repetition-chain closed forms, exhaustive ML
 on small codes, the coset-symmetry invariant and the noiseless limit
@@ -56,6 +60,9 @@ def _load():
             lib.oracle_decode.restype = ctypes.c_int
             lib.oracle_decode.argtypes = [i32, i32, i64, ptr, ptr, i32, ptr, ptr,
                                           i32, i32, dbl, ptr, ptr, ptr, ptr, i32]
+            lib.oracle_wbp.restype = ctypes.c_int
+            lib.oracle_wbp.argtypes = [i32, i32, i64, ptr, ptr, ptr, i32, i32, ptr, ptr, ptr, i32, ptr, dbl,
+                                       ptr, ptr, ptr, ptr, i32]
             lib.oracle_syndrome_ok.restype = ctypes.c_int
             lib.oracle_syndrome_ok.argtypes = [i32, i32, i64, ptr, ptr, i32, ptr, ptr, ptr]
             _lib = lib
@@ -119,6 +126,33 @@ def decode(graph, llr: np.ndarray, syndrome: np.ndarray, iters: int,
 def decode_y(graph, y: np.ndarray, sigma, syndrome: np.ndarray, iters: int, **kw):
     """Decode from the channel observation y with per-codeword sigma."""
     return decode(graph, channel_llr(y, sigma), syndrome, iters, **kw)
+
+
+def wbp(graph, llr: np.ndarray, syndrome: np.ndarray, xbits: np.ndarray, weights: np.ndarray,
+        edge_type=None, lmax: float = LMAX, threads: int | None = None):
+    """Weighted BP (weights [T, n_types] on the variable-to-check messages)
+    with the mean-BCE loss against the true bits, and its exact gradient.
+
+    Returns dict(loss, post [B, n], dw [T, n_types], dllr [B, n]).
+    """
+    n, m, ev, ec = _edges(graph)
+    et = np.ascontiguousarray(graph.edge_type if edge_type is None else edge_type, dtype=np.uint8)
+    W = np.ascontiguousarray(weights, dtype=np.float64)
+    T, nt = W.shape
+    L = np.ascontiguousarray(np.atleast_2d(llr), dtype=np.float64)
+    S = np.ascontiguousarray(np.atleast_2d(syndrome), dtype=np.uint8)
+    X = np.ascontiguousarray(np.atleast_2d(xbits), dtype=np.uint8)
+    B = L.shape[0]
+    loss = np.zeros(1)
+    post = np.zeros((B, n))
+    dw = np.zeros((T, nt))
+    dllr = np.zeros((B, n))
+    st = _load().oracle_wbp(n, m, ev.shape[0], _p(ev), _p(ec), _p(et), nt, B, _p(L), _p(S), _p(X), T,
+                            _p(W), float(lmax), _p(loss), _p(post), _p(dw), _p(dllr),
+                            int(threads or default_threads()))
+    if st != 0:
+        raise RuntimeError(f"oracle_wbp failed with status {st}")
+    return dict(loss=float(loss[0]), post=post, dw=dw, dllr=dllr)
 
 
 def syndrome_ok(graph, bits: np.ndarray, syndrome: np.ndarray) -> np.ndarray:

@@ -267,3 +267,198 @@ int oracle_syndrome_ok(int32_t n_vn, int32_t n_cn, int64_t n_edges,
     adj_free(&a);
     return ORACLE_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Weighted BP and its exact gradient (reverse mode, full history).           */
+/*                                                                           */
+/* Weighted BP scales each variable-to-check message by a weight that depends */
+/* on the iteration t and on the edge's type tau(e):                          */
+/*   x_e^t = Lch(v) + sum_{c' in C_v \ c} r_{c'->v}^{t-1}                     */
+/*   q_e^t = clamp(w[t][tau(e)] * x_e^t)                                      */
+/*   r_e^t = check update of the q^t as in plain BP (Eqs. 2-3, syndrome sign) */
+/*   L_v   = Lch(v) + sum_{c in C_v} r^T                                       */
+/*   loss  = mean_{b,v} softplus(-(1 - 2 x_v) L_v)                            */
+/* All weights equal to 1 is plain BP.  Derivatives of the clamps are 1      */
+/* strictly inside and 0 outside; the sign factors have derivative 0;         */
+/* phi'(x) = -1/sinh(x).                                                       */
+/* ------------------------------------------------------------------------- */
+
+static double softplus(double z) { return z > 0 ? z + log1p(exp(-z)) : log1p(exp(z)); }
+static double sigmoid(double z) { return z >= 0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z)); }
+
+typedef struct {
+    const adjacency *a;
+    const uint8_t *etype;  /* [E] */
+    int32_t n_types;
+    const double *llr;     /* [B][n] */
+    const uint8_t *syn;    /* [B][m] */
+    const uint8_t *xbits;  /* [B][n] */
+    int32_t batch, T;
+    const double *w;       /* [T][n_types] */
+    double lmax;
+    double *loss;          /* [B]: per-codeword sum of softplus terms */
+    double *post;          /* [B][n] */
+    double *dw;            /* [B][T][n_types] per-codeword partial */
+    double *dllr;          /* [B][n] */
+    int next, status;
+} wbp_job;
+
+static int wbp_one(const wbp_job *J, int b) {
+    const adjacency *a = J->a;
+    const int32_t n = a->n_vn;
+    const int64_t E = a->n_edges;
+    const int T = J->T, NT = J->n_types;
+    const double lmax = J->lmax, amin = oracle_phi(lmax);
+    const double *llr = J->llr + (size_t)b * n;
+    const uint8_t *s = J->syn + (size_t)b * a->n_cn;
+    const uint8_t *xb = J->xbits + (size_t)b * n;
+    const size_t Es = (size_t)(E > 0 ? E : 1);
+    double *Lch = calloc((size_t)n + 1, sizeof(double));
+    double *gLch = calloc((size_t)n + 1, sizeof(double));
+    double *r = calloc(Es * (size_t)(T + 1), sizeof(double));   /* r[t][e], r[0] = 0 */
+    double *x = calloc(Es * (size_t)(T + 1), sizeof(double));   /* x[t][e] */
+    double *gr = calloc(Es, sizeof(double));                     /* dloss/dr^t */
+    double *gx = calloc(Es, sizeof(double));
+    double *q = calloc(Es, sizeof(double)), *f = calloc(Es, sizeof(double));
+    double *go = calloc(Es, sizeof(double));
+    double *dw = J->dw + (size_t)b * T * NT;
+    if (!Lch || !gLch || !r || !x || !gr || !gx || !q || !f || !go) {
+        free(Lch); free(gLch); free(r); free(x); free(gr); free(gx); free(q); free(f); free(go);
+        return ORACLE_ENOMEM;
+    }
+    for (int32_t v = 0; v < n; ++v) Lch[v] = clampd(llr[v], -lmax, lmax);
+
+    /* forward, keeping x^t and r^t for every iteration */
+    for (int t = 1; t <= T; ++t) {
+        double *rp = r + (size_t)(t - 1) * Es, *rt = r + (size_t)t * Es, *xt = x + (size_t)t * Es;
+        for (int32_t v = 0; v < n; ++v)
+            for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) {
+                double acc = Lch[v];
+                for (int64_t k2 = a->vptr[v]; k2 < a->vptr[v + 1]; ++k2)
+                    if (k2 != k) acc += rp[a->vedge[k2]];
+                xt[a->vedge[k]] = acc;
+            }
+        for (int64_t e = 0; e < E; ++e) {
+            q[e] = clampd(J->w[(size_t)(t - 1) * NT + J->etype[e]] * xt[e], -lmax, lmax);
+            f[e] = oracle_phi(clampd(fabs(q[e]), amin, lmax));
+        }
+        for (int32_t c = 0; c < a->n_cn; ++c)
+            for (int64_t k = a->cptr[c]; k < a->cptr[c + 1]; ++k) {
+                double sgn = (s[c] & 1) ? -1.0 : 1.0, sum = 0.0;
+                for (int64_t k2 = a->cptr[c]; k2 < a->cptr[c + 1]; ++k2) {
+                    if (k2 == k) continue;
+                    if (q[a->cedge[k2]] < 0.0) sgn = -sgn;
+                    sum += f[a->cedge[k2]];
+                }
+                rt[a->cedge[k]] = clampd(sgn * oracle_phi(clampd(sum, amin, lmax)), -lmax, lmax);
+            }
+    }
+    double lsum = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+        double L = Lch[v];
+        for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) L += r[(size_t)T * Es + a->vedge[k]];
+        if (J->post) J->post[(size_t)b * n + v] = L;
+        const double y = 1.0 - 2.0 * (xb[v] & 1);
+        lsum += softplus(-y * L);
+        /* d softplus(-yL)/dL = -y sigmoid(-yL); the loss is a mean over B*n */
+        const double g = -y * sigmoid(-y * L) / ((double)J->batch * (double)n);
+        gLch[v] += g;
+        for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) gr[a->vedge[k]] = g;
+    }
+    J->loss[b] = lsum;
+
+    /* reverse sweep */
+    for (int t = T; t >= 1; --t) {
+        const double *rp = r + (size_t)(t - 1) * Es, *xt = x + (size_t)t * Es;
+        (void)rp;
+        for (int64_t e = 0; e < E; ++e) {
+            q[e] = clampd(J->w[(size_t)(t - 1) * NT + J->etype[e]] * xt[e], -lmax, lmax);
+            f[e] = oracle_phi(clampd(fabs(q[e]), amin, lmax));
+        }
+        /* r_e = sgn_e * phi(clamp(o_e)), o_e = sum of the other f */
+        for (int32_t c = 0; c < a->n_cn; ++c)
+            for (int64_t k = a->cptr[c]; k < a->cptr[c + 1]; ++k) {
+                const int64_t e = a->cedge[k];
+                double sgn = (s[c] & 1) ? -1.0 : 1.0, o = 0.0;
+                for (int64_t k2 = a->cptr[c]; k2 < a->cptr[c + 1]; ++k2) {
+                    if (k2 == k) continue;
+                    if (q[a->cedge[k2]] < 0.0) sgn = -sgn;
+                    o += f[a->cedge[k2]];
+                }
+                /* |r| = phi(clamp(o)) <= lmax: the outer clamp never binds */
+                go[e] = (o > amin && o < lmax) ? sgn * gr[e] * (-1.0 / sinh(o)) : 0.0;
+            }
+        for (int64_t e = 0; e < E; ++e) gx[e] = 0.0;
+        for (int32_t c = 0; c < a->n_cn; ++c)
+            for (int64_t k = a->cptr[c]; k < a->cptr[c + 1]; ++k) {
+                const int64_t e = a->cedge[k];
+                double gf = 0.0;
+                for (int64_t k2 = a->cptr[c]; k2 < a->cptr[c + 1]; ++k2)
+                    if (k2 != k) gf += go[a->cedge[k2]];
+                const double aq = fabs(q[e]);
+                const double ga = (aq > amin && aq < lmax) ? gf * (-1.0 / sinh(aq)) : 0.0;
+                const double gq = q[e] > 0 ? ga : (q[e] < 0 ? -ga : 0.0);
+                const double wt = J->w[(size_t)(t - 1) * NT + J->etype[e]];
+                const double p = wt * xt[e];
+                const double gp = (p > -lmax && p < lmax) ? gq : 0.0;
+                dw[(size_t)(t - 1) * NT + J->etype[e]] += gp * xt[e];
+                gx[e] = gp * wt;
+            }
+        /* x_e = Lch(v) + sum of the other r^{t-1} at v */
+        for (int64_t e = 0; e < E; ++e) gr[e] = 0.0;
+        for (int32_t v = 0; v < n; ++v)
+            for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) {
+                const int64_t e = a->vedge[k];
+                gLch[v] += gx[e];
+                for (int64_t k2 = a->vptr[v]; k2 < a->vptr[v + 1]; ++k2)
+                    if (k2 != k) gr[a->vedge[k2]] += gx[e];
+            }
+    }
+    for (int32_t v = 0; v < n; ++v)
+        J->dllr[(size_t)b * n + v] = (llr[v] > -lmax && llr[v] < lmax) ? gLch[v] : 0.0;
+    free(Lch); free(gLch); free(r); free(x); free(gr); free(gx); free(q); free(f); free(go);
+    return ORACLE_OK;
+}
+
+static void *wbp_worker(void *arg) {
+    wbp_job *J = arg;
+    for (;;) {
+        int b = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (b >= J->batch) break;
+        int st = wbp_one(J, b);
+        if (st != ORACLE_OK) __atomic_store_n(&J->status, st, __ATOMIC_RELAXED);
+    }
+    return NULL;
+}
+
+/* loss (mean over B*n), posteriors, dloss/dw [T][n_types], dloss/dllr [B][n] */
+int oracle_wbp(int32_t n_vn, int32_t n_cn, int64_t n_edges, const int32_t *edge_vn,
+               const int32_t *edge_cn, const uint8_t *edge_type, int32_t n_types,
+               int32_t batch, const double *llr, const uint8_t *syndrome, const uint8_t *xbits,
+               int32_t T, const double *w, double lmax, double *loss, double *post,
+               double *dw, double *dllr, int32_t n_threads) {
+    if (n_vn < 0 || n_cn < 0 || n_edges < 0 || batch < 1 || T < 1 || n_types < 1 || !(lmax > 0.0))
+        return ORACLE_EINVAL;
+    for (int64_t e = 0; e < n_edges; ++e)
+        if (edge_type[e] >= n_types) return ORACLE_EINVAL;
+    adjacency a;
+    int st = adj_build(&a, n_vn, n_cn, n_edges, edge_vn, edge_cn);
+    if (st != ORACLE_OK) return st;
+    double *lossb = calloc((size_t)batch, sizeof(double));
+    double *dwb = calloc((size_t)batch * T * n_types, sizeof(double));
+    if (!lossb || !dwb) { free(lossb); free(dwb); adj_free(&a); return ORACLE_ENOMEM; }
+    wbp_job J = {&a, edge_type, n_types, llr, syndrome, xbits, batch, T, w, lmax,
+                 lossb, post, dwb, dllr, 0, ORACLE_OK};
+    st = run_workers(wbp_worker, &J, n_threads, batch);
+    double l = 0.0;
+    for (int32_t b = 0; b < batch; ++b) l += lossb[b];
+    *loss = l / ((double)batch * (double)n_vn);
+    for (int64_t i = 0; i < (int64_t)T * n_types; ++i) {
+        double acc = 0.0;
+        for (int32_t b = 0; b < batch; ++b) acc += dwb[(size_t)b * T * n_types + i];
+        dw[i] = acc;
+    }
+    free(lossb); free(dwb);
+    adj_free(&a);
+    return st != ORACLE_OK ? st : J.status;
+}
