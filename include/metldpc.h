@@ -223,6 +223,39 @@ int mld_plan_destroy(mld_plan *p);
 /* Create a plan, launch it on `stream`, wait for the stream, destroy it. */
 int mld_decode_multi(const mld_job *jobs, int32_t n_jobs, uint32_t flags, void *stream);
 
+/* ---- differentiable weighted BP --------------------------------------------
+ * Weighted BP scales every variable-to-check message of iteration t by a
+ * learnable weight w[t][type(e)] (type = the edge_type given at graph
+ * creation): in the LLR form of Methods Eq. 4,
+ *   q_e^t = clamp(w[t][type(e)] * (L_ch(v) + sum_{e' != e} r_{e'}^{t-1})),
+ * followed by the check update of Eqs. 2-3 (syndrome sign, phi, clamps);
+ * all weights 1 is plain BP.  The soft output is the posterior of Eq. 5
+ * after T iterations.  The adjoint gives dloss/dw and dloss/dLLR for any
+ * loss of the soft output; it recomputes segments of ckpt_k iterations from
+ * messages stored every ckpt_k iterations (ckpt_k = 1 stores every one).
+ *
+ * mld_wbp_forward:
+ *   d        : decoder with MLD_MSG_F32 storage (its working memory is used;
+ *              no other call may use d until the tape is destroyed).
+ *   llr      : device float [batch][n_vn] channel LLRs (clamped to lmax).
+ *   syndrome : device uint8 [batch][n_cn].   1 <= batch <= max_batch.
+ *   w        : device float [T][n_types], 1 <= n_types <= MLD_MAX_EDGE_TYPES,
+ *              every edge type of the graph < n_types.
+ *   T >= 1 iterations; ckpt_k >= 1.
+ *   soft_out : device float [batch][n_vn] posteriors after iteration T.
+ *   tape     : receives the tape for mld_wbp_backward, or NULL (no tape).
+ * mld_wbp_backward: dsoft = dloss/dsoft_out (device float [batch][n_vn]);
+ *   writes dw (device float [T][n_types]) and dllr (device float
+ *   [batch][n_vn], 0 where the LLR was clamped).  May be called more than once.
+ * Checks of degree above 16 are refused (MLD_EINVAL).  Errors: MLD_EINVAL,
+ * MLD_ENOMEM, MLD_ECUDA. */
+typedef struct mld_tape mld_tape;
+int mld_wbp_forward(mld_decoder *d, const float *llr, const uint8_t *syndrome, int32_t batch,
+                    const float *w, int32_t n_types, int32_t T, int32_t ckpt_k,
+                    float *soft_out, mld_tape **tape, void *stream);
+int mld_wbp_backward(mld_tape *t, const float *dsoft, float *dw, float *dllr, void *stream);
+int mld_tape_destroy(mld_tape *t);
+
 /* ---- kernel timing (measurement hook) -------------------------------------
  * With timing enabled, every later decode call on d records a pair of CUDA
  * events on its stream around each kernel it launches.  mld_decoder_timing_read

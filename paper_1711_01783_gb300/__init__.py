@@ -33,7 +33,8 @@ EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destr
            "mld_graph_stats_get", "mld_decoder_create", "mld_decoder_destroy", "mld_decode",
            "mld_decode_y", "mld_decode_status", "mld_decoder_timing_enable",
            "mld_decoder_timing_read", "mld_decode_noalloc", "mld_plan_create", "mld_plan_launch",
-           "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_phi_eval")
+           "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_wbp_forward", "mld_wbp_backward",
+           "mld_tape_destroy", "mld_phi_eval")
 
 
 class MldError(RuntimeError):
@@ -93,6 +94,9 @@ def _load() -> ctypes.CDLL:
         "mld_plan_stats": (ctypes.c_int, [P, ctypes.POINTER(I64)]),
         "mld_plan_destroy": (ctypes.c_int, [P]),
         "mld_decode_multi": (ctypes.c_int, [P, I32, U32, P]),
+        "mld_wbp_forward": (ctypes.c_int, [P, P, P, I32, P, I32, I32, I32, P, ctypes.POINTER(P), P]),
+        "mld_wbp_backward": (ctypes.c_int, [P, P, P, P, P]),
+        "mld_tape_destroy": (ctypes.c_int, [P]),
         "mld_phi_eval": (ctypes.c_int, [I32, P, P, I64, P]),
     }
     for name, (res, args) in sig.items():
@@ -284,6 +288,20 @@ class Decoder:
     def status(self) -> int:
         return int(lib().mld_decode_status(self._h))
 
+    def wbp_forward(self, llr, syndrome, weights, ckpt_k: int = 5, keep_tape: bool = True, stream=None):
+        """Weighted BP forward (mld_wbp_forward); returns (soft [B, n], Tape or None)."""
+        torch = _torch()
+        llr = llr.contiguous().to(torch.float32)
+        syndrome = syndrome.contiguous().to(torch.uint8)
+        w = weights.detach().contiguous().to(torch.float32)
+        T, nt = int(w.shape[0]), int(w.shape[1])
+        soft = torch.empty_like(llr)
+        h = ctypes.c_void_p()
+        _check(lib().mld_wbp_forward(self._h, _ptr(llr), _ptr(syndrome), int(llr.shape[0]), _ptr(w), nt, T,
+                                     int(ckpt_k), _ptr(soft), ctypes.byref(h) if keep_tape else None,
+                                     _stream_handle(stream)))
+        return soft, (Tape(h, self, llr.shape, (T, nt)) if keep_tape else None)
+
     def timing(self, enable: bool):
         """Record CUDA events around each kernel of later decode calls."""
         _check(lib().mld_decoder_timing_enable(self._h, int(bool(enable))))
@@ -293,6 +311,56 @@ class Decoder:
         t = Timing()
         _check(lib().mld_decoder_timing_read(self._h, ctypes.byref(t)))
         return {f: getattr(t, f) for f, _ in Timing._fields_}
+
+
+class Tape:
+    """Recorded forward of weighted BP, for mld_wbp_backward."""
+
+    def __init__(self, handle, decoder, llr_shape, w_shape):
+        self._h = handle
+        self.decoder = decoder
+        self.llr_shape = tuple(llr_shape)
+        self.w_shape = tuple(w_shape)
+
+    def backward(self, dsoft, stream=None):
+        torch = _torch()
+        dsoft = dsoft.contiguous().to(torch.float32)
+        dw = torch.empty(self.w_shape, dtype=torch.float32, device=dsoft.device)
+        dllr = torch.empty(self.llr_shape, dtype=torch.float32, device=dsoft.device)
+        _check(lib().mld_wbp_backward(self._h, _ptr(dsoft), _ptr(dw), _ptr(dllr), _stream_handle(stream)))
+        return dw, dllr
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mld_tape_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def weighted_bp(decoder, llr, syndrome, weights, ckpt_k: int = 5):
+    """Differentiable weighted BP: soft posteriors [B, n] as a function of the
+    channel LLRs and the weights [T, n_types] (torch.autograd)."""
+    torch = _torch()
+
+    class _WeightedBP(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, llr_, w_):
+            soft, tape = decoder.wbp_forward(llr_, syndrome, w_, ckpt_k=ckpt_k)
+            ctx.tape = tape
+            return soft
+
+        @staticmethod
+        def backward(ctx, dsoft):
+            dw, dllr = ctx.tape.backward(dsoft)
+            ctx.tape.close()
+            return dllr, dw
+
+    return _WeightedBP.apply(llr, weights)
 
 
 class Plan:
@@ -387,5 +455,5 @@ def phi(x, msg_dtype: str = "f32", stream=None):
     return out
 
 
-__all__ = ["Graph", "Decoder", "Plan", "phi", "decode_noalloc", "version", "lib", "MldError", "EXPORTS",
+__all__ = ["Graph", "Decoder", "Plan", "Tape", "weighted_bp", "phi", "decode_noalloc", "version", "lib", "MldError", "EXPORTS",
            "LIB_PATH", "NOALLOC_SCRATCH_BYTES"]
