@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="fixed", choices=["fixed", "uneven"],
+    ap.add_argument("--train-steps", type=int, default=60)
+    ap.add_argument("--workload", default="fixed", choices=["fixed", "uneven", "wbp"],
                     help="fixed: one code, fixed iterations (the headline); uneven: 96 codewords over "
                          "rates 0.1/0.05/0.02 and n in {2^16, 2^18, 10^6}, caps 100/150/200, early "
                          "termination, one captured plan")
@@ -262,8 +263,102 @@ def run_uneven(a, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_wbp(a, world, rank, local):
+    """Weighted BP: train the per-(iteration, edge type) weights on decoder-
+    generated samples (rate 0.1, n = 10^5, 16 codewords, T = 20, checkpoint
+    every 5), then compare the frame error rate of the trained and the unit
+    weights (plain BP) at n = 10^6.  value = training throughput (codeword
+    bits through forward + adjoint per second)."""
+    import torch
+    import paper_1711_01783_gb300 as mld
+    from synthetic import make_workload, preset_graph
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n_tr, B_tr, T, k = 100_000, 16, 20, 5
+    beta = a.beta
+    g_tr = preset_graph(0.1, n_tr, 10)
+    G_tr = mld.Graph.from_edges(g_tr)
+    dec = mld.Decoder(G_tr, B_tr, msg_dtype="f32", slab_width=16)
+
+    def batch(seed):
+        wl = make_workload(0.1, n_tr, B_tr, 10, seed, beta=beta, graph=g_tr)
+        llr = torch.from_numpy(2.0 * wl.y / (wl.sigma[:, None] ** 2)).to(dev)
+        y = 1.0 - 2.0 * torch.from_numpy(wl.x.astype(np.float32)).to(dev)
+        return llr, torch.from_numpy(wl.s).to(dev), y
+
+    data = [batch(20_000 + i) for i in range(16)]
+    val = batch(40_000)
+    wt = torch.ones((T, 3), device=dev, requires_grad=True)
+    opt = torch.optim.Adam([wt], lr=0.01)
+    losses = []
+
+    def val_loss():
+        with torch.no_grad():
+            soft, _ = dec.wbp_forward(val[0], val[1], wt.detach(), keep_tape=False)
+            return float(torch.nn.functional.softplus(-val[2] * soft).mean())
+
+    val_before = val_loss()
+
+    def step(i):
+        llr, s, y = data[i % len(data)]
+        opt.zero_grad()
+        soft = mld.weighted_bp(dec, llr, s, wt, ckpt_k=k)
+        loss = torch.nn.functional.softplus(-y * soft).mean()
+        loss.backward()
+        opt.step()
+        return loss
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(a.train_steps):
+        losses.append(step(a.warmup + i))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.train_steps
+    losses = [float(x.detach()) for x in losses]
+    val_after = val_loss()
+
+    # judge: FER at n = 10^6 of unit weights (plain BP) and of the trained weights
+    n_ev, B_ev = 1_000_000, 64
+    wl = make_workload(0.1, n_ev, B_ev, 11, 30_000, beta=beta)
+    G_ev = mld.Graph.from_edges(wl.graph)
+    dec_ev = mld.Decoder(G_ev, B_ev, msg_dtype="f32")
+    llr = torch.from_numpy(2.0 * wl.y / (wl.sigma[:, None] ** 2)).to(dev)
+    s = torch.from_numpy(wl.s).to(dev)
+    x = torch.from_numpy(wl.x).to(dev)
+    fer = {}
+    for name, wv in (("plain", torch.ones((T, 3), device=dev)), ("weighted", wt.detach())):
+        soft, _ = dec_ev.wbp_forward(llr, s, wv, keep_tape=False)
+        bits = (soft < 0).to(torch.uint8)
+        fer[name] = float((bits != x).any(dim=1).float().mean())
+    line = {
+        "metric": "weighted-BP training throughput (forward + adjoint), codeword bits per second",
+        "value": B_tr * n_tr / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world, "steps": a.train_steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MET ensemble, BIAWGN samples)",
+        "config": {"workload": f"rate 0.1, n={n_tr}, {B_tr} codewords, T={T}, checkpoint every {k}, "
+                               f"20x3 weights, Adam lr 0.01, beta={beta}; judged at n={n_ev}, {B_ev} codewords"},
+        "val_loss_unit_weights": val_before, "val_loss_trained": val_after,
+        "train_loss_first5": float(np.mean(losses[:5])), "train_loss_last5": float(np.mean(losses[-5:])),
+        "fer_plain_T20": fer["plain"], "fer_weighted_T20": fer["weighted"],
+        "weights_mean_per_type": wt.detach().mean(dim=0).tolist(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.workload == "wbp":
+        if a.beta == 0.90:
+            a.beta = 0.40
+        run_wbp(a, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+                int(os.environ.get("LOCAL_RANK", "0")))
+        return
     if a.workload == "uneven":
         if a.batch == 64:
             a.batch = 96
