@@ -22,7 +22,7 @@ const char *last_error_text();
 namespace {
 
 constexpr int kK = 4;          // codewords per thread
-constexpr int kBlock = 256;
+constexpr int kBlock = 128;
 
 // ---------------------------------------------------------------------------
 // phi(x) = -ln tanh(x/2) in float, for x in [phi(lmax), lmax].
@@ -268,8 +268,12 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             const float4 lv = ldf4(lvb + static_cast<size_t>(vidx[i]) * W);
             const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
             const float4 q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
-            const float4 m = make_float4(clampf(fabsf(q.x), amin, lmax), clampf(fabsf(q.y), amin, lmax),
-                                         clampf(fabsf(q.z), amin, lmax), clampf(fabsf(q.w), amin, lmax));
+            // |q| is clamped above only: an argument below phi(lmax) gives a
+            // phi term above lmax (up to +inf at 0), which clamps every other
+            // term's leave-one-out sum to lmax exactly as the clamped term
+            // would; terms are only added, so no inf - inf arises
+            const float4 m = make_float4(fminf(fabsf(q.x), lmax), fminf(fabsf(q.y), lmax),
+                                         fminf(fabsf(q.z), lmax), fminf(fabsf(q.w), lmax));
             const float4 ph = phi4<H>(m);
 #pragma unroll
             for (int kk = 0; kk < kK; ++kk) {
@@ -394,7 +398,7 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
 // One check class per launch, its shape (DC, DD) a compile-time constant: the
 // register arrays are sized exactly and only this class's code is hot.
 template <typename MsgT, int W, int DC, int DD>
-__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 4 : 3)) k_check_update(CnArgs a, ClassLaunch cl) {
+__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
     check_regular<MsgT, W, DC, DD>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, slab);

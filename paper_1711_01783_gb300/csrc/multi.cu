@@ -46,7 +46,7 @@ __device__ __forceinline__ int find_seg(const Seg *segs, int nseg) {
 }
 
 template <typename MsgT, int W, int DC, int DD>
-__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 4 : 3))
+__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6))
     km_check(const JobDev *jobs, const Seg *segs, int nseg) {
     const Seg sg = segs[find_seg(segs, nseg)];
     CnArgs a = jobs[sg.job].cn;
