@@ -109,7 +109,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
               d->lmax, d->amin, 0, et ? 1 : 0};
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
-               d->fail, d->done, et ? 1 : 0};
+               d->fail, d->done, et ? 1 : 0, batch};
     // check-update launches, one per check class (built with the graph)
     const int wi = W == 8 ? 0 : (W == 16 ? 1 : (W == 32 ? 2 : 3));
     const std::vector<ClassLaunch> &launches = g->launches[wi];
@@ -117,7 +117,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, d->device);
     const int64_t syn_threads = static_cast<int64_t>(h.n_cn) * (W / 8);
-    const int syn_blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid_x(syn_threads), 4LL * sm_count)));
+    const int syn_blocks = static_cast<int>(std::max<int64_t>(1, grid_x(syn_threads)));
     const dim3 syn_grid(syn_blocks, slabs);
     const int lane_blocks = (batch + 127) / 128;
 

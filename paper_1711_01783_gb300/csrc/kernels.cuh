@@ -502,6 +502,7 @@ struct SynArgs {
     uint32_t *fail;
     const uint32_t *done;
     int et;
+    int32_t batch;         // codewords in the batch (later lanes are padding)
 };
 
 // Threads first, first + stride, ... of the (check, byte) index space of one
@@ -514,19 +515,33 @@ __device__ __forceinline__ void syndrome_body(const SynArgs &a, int64_t first, i
     const size_t cbase = static_cast<size_t>(slab) * a.n_cn;
     const uint8_t *hc = a.hb_core + static_cast<size_t>(slab) * a.n_core * NB + g;
     const uint8_t *h1 = a.hb1 + static_cast<size_t>(slab) * a.n_deg1 * NB + g;
+    uint32_t *fw = a.fail + slab * DW + (g * 8) / 32;
+    const int sh = (g * 8) & 31;
+    // codewords whose outcome is already known: frozen (early termination)
+    // or padding lanes past the end of the batch
+    uint32_t known = a.et ? ((a.done[slab * DW + (g * 8) / 32] >> sh) & 0xFFu) : 0u;
+    const int first_lane = slab * W + g * 8;
+    if (first_lane + 8 > a.batch)
+        known |= (0xFFu << max(0, min(8, a.batch - first_lane))) & 0xFFu;
     uint32_t acc = 0;
     const int64_t total = static_cast<int64_t>(a.n_cn) * NB;
     for (int64_t t = first; t < total; t += stride) {
+        // once each of this byte's 8 codewords has failed a check (or is
+        // frozen), further checks cannot change the result
+        if ((acc | known) == 0xFFu) break;
         const int32_t c = static_cast<int32_t>(t / NB);
         uint32_t x = a.sbits[(cbase + c) * NB + g];
         for (int32_t e = a.cptr[c]; e < a.cptr[c + 1]; ++e) x ^= hc[static_cast<size_t>(__ldg(a.col + e)) * NB];
         for (int32_t s = a.dptr[c]; s < a.dptr[c + 1]; ++s) x ^= h1[static_cast<size_t>(s) * NB];
         acc |= x;
     }
+    acc &= ~known;
 #pragma unroll
     for (int o = 16; o >= NB; o >>= 1) acc |= __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-    if ((threadIdx.x & 31) < NB && acc)
-        atomicOr(a.fail + slab * DW + (g * 8) / 32, acc << ((g * 8) & 31));
+    // set only bits not already set: most warps of a failing slab then read
+    // the word instead of contending on it
+    if ((threadIdx.x & 31) < NB && acc && ((*reinterpret_cast<volatile uint32_t *>(fw) >> sh) & acc) != acc)
+        atomicOr(fw, acc << sh);
 }
 
 template <int W>

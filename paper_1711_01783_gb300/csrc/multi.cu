@@ -252,7 +252,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
         x.vn = VnArgs{d->g->vptr, d->g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0,
                       et ? 1 : 0};
         x.sy = SynArgs{d->g->cptr, d->g->col, d->g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core,
-                       d->hb1, d->fail, d->done, et ? 1 : 0};
+                       d->hb1, d->fail, d->done, et ? 1 : 0, jb.batch};
         x.in = InArgs{jb.in, y_mode ? jb.sigma : nullptr, d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch,
                       d->lmax, d->amin, d->lch, d->Lv, d->lch1, d->post1, d->phi1};
         x.out = OutArgs{d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch, d->Lv, d->post1, jb.bits_out,
@@ -342,7 +342,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
         for (int32_t j : js) {
             const mld_decoder *d = jobs[j].decoder;
             const int64_t work = static_cast<int64_t>(jd[j].n_cn) * (d->W / 8);
-            const int bps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid_x(work), 256)));
+            const int bps = static_cast<int>(std::max<int64_t>(1, grid_x(work)));
             if (jd[j].n_cn > 0) groups[Key{kOpSyn, 0, d->W, 0, 0}].push_back(seg(j, bps, jd[j].slabs, 0));
         }
         flush(groups, l, parity);
