@@ -85,6 +85,28 @@ def workload_config(a) -> dict:
     }
 
 
+def rank_data_seed(rank: int) -> int:
+    """Replicas decode different codewords: rank r draws data seed 1000 + 64 r."""
+    return 1000 + 64 * rank
+
+
+def reduce_over_ranks(dist, ms: float, launches: int, device) -> tuple[float, int]:
+    """Max of the timed region over ranks (the slowest replica sets the job
+    time) and the sum of kernel launches; identity without a process group."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    n = torch.tensor([launches], dtype=torch.int64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
+def job_throughput(world: int, batch: int, n: int, steps: int, ms_max: float) -> float:
+    """Whole-job decoded Mbit/s: all ranks' bits over the slowest rank's time."""
+    return world * batch * n * steps / (ms_max * 1e-3) / 1e6
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -393,7 +415,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    wl = make_workload(a.rate, a.n, a.batch, seed_graph, 1000 + 64 * rank, beta=a.beta)
+    wl = make_workload(a.rate, a.n, a.batch, seed_graph, rank_data_seed(rank), beta=a.beta)
     g = mld.Graph.from_edges(wl.graph)
     dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, slab_width=a.slab)
     st = g.stats
@@ -439,15 +461,9 @@ def main():
     dec.timing(False)
     kt = dec.read_timing()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    launches = torch.tensor([kt["check_launches"] + kt["var_launches"] + kt["syndrome_launches"]
-                             + kt["layout_launches"]], dtype=torch.int64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(launches, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    bits_total = world * a.batch * a.n * a.steps
-    value = bits_total / (ms_max * 1e-3) / 1e6
+    ms_max, launches = reduce_over_ranks(dist, ms, kt["check_launches"] + kt["var_launches"]
+                                         + kt["syndrome_launches"] + kt["layout_launches"], dev)
+    value = job_throughput(world, a.batch, a.n, a.steps, ms_max)
 
     # ---- end to end through the host-pointer path ---------------------------
     e2e = None
@@ -509,7 +525,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded MET ensemble, BIAWGN samples)", "config": workload_config(a),
-            "e2e": e2e, "gpu_launches": int(launches.item()), "roofline": roofline,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk,
             "frames_converged": int(out["converged"].sum().item()),
         }
