@@ -88,11 +88,11 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     if (rbytes) MLD_CUDA(cudaMemsetAsync(d->r, 0, rbytes, st));
     MLD_CUDA(cudaMemsetAsync(d->done, 0, sizeof(uint32_t) * slabs * DW, st));
 
-    InArgs ia{in, sigma, g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->lmax, d->amin,
+    InArgs ia{in, sigma, g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->lmax, d->scale_in, d->lmax_i, d->amin_i,
               d->lch, d->Lv, d->lch1, d->post1, d->phi1};
     if (h.n_vn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_interleave_in", [&] {
-            k_interleave_in<W, IsHalf<MsgT>::value><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(ia);
+            k_interleave_in<W, DecodeFit<MsgT>::value><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(ia);
         });
         if (s != MLD_OK) return s;
     }
@@ -106,7 +106,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
 
     CnArgs ca{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, h.e_core,
               d->r, d->Lv, d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done,
-              d->lmax, d->amin, 0, et ? 1 : 0};
+              d->lmax_i, d->amin_i, 0, et ? 1 : 0};
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
                d->fail, d->done, et ? 1 : 0, batch};
@@ -175,7 +175,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         }
     }
 
-    OutArgs oa{g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, bits, post};
+    OutArgs oa{g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, bits, post, d->scale_out};
     if (h.n_vn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_deinterleave_out", [&] {
             k_deinterleave_out<W><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(oa);
@@ -342,8 +342,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     d->W = W;
     d->max_batch = opts->max_batch;
     d->max_slabs = (opts->max_batch + W - 1) / W;
-    d->lmax = opts->lmax > 0.f ? opts->lmax : 25.f;
-    d->amin = static_cast<float>(phi_host(static_cast<double>(d->lmax)));
+    set_units(d, opts->lmax > 0.f ? opts->lmax : 25.f);
     const mld::HostGraph &h = g->h;
     const size_t S = d->max_slabs;
     const size_t msz = d->msg == MLD_MSG_F16 ? 2 : 4;
@@ -453,10 +452,17 @@ int mld_phi_eval(int32_t msg_dtype, const float *x, float *out, int64_t n, void 
     if (n == 0) return MLD_OK;
     const float lmax = 25.f;
     const float amin = static_cast<float>(phi_host(25.0));
+    const float kLog2e = 1.442695040888963407f, kLn2 = 0.693147180559945309f;
+    const float lmax_i = static_cast<float>(25.0 * 1.4426950408889634074);
+    const float amin_i = static_cast<float>(phi_host(25.0) * 1.4426950408889634074);
     if (msg_dtype == MLD_MSG_F16)
-        k_phi_eval<true><<<grid_x(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n, lmax, amin);
+        k_phi_eval<kFitB2H><<<grid_x(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n, kLog2e, lmax_i,
+                                                                                     amin_i, kLn2);
     else
-        k_phi_eval<false><<<grid_x(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n, lmax, amin);
+        k_phi_eval<kFitB2><<<grid_x(n), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n, kLog2e, lmax_i,
+                                                                                    amin_i, kLn2);
+    (void)lmax;
+    (void)amin;
     MLD_LAUNCHED("k_phi_eval");
     return MLD_OK;
 }
@@ -561,8 +567,7 @@ extern "C" int mld_decode_noalloc(const mld_graph *g, int32_t msg_dtype, const f
     d.W = W;
     d.max_batch = batch;
     d.max_slabs = slabs;
-    d.lmax = 25.f;
-    d.amin = static_cast<float>(phi_host(25.0));
+    set_units(&d, 25.f);
     d.r = base + L.r;
     d.Lv = reinterpret_cast<float *>(base + L.Lv);
     d.lch = reinterpret_cast<float *>(base + L.lch);

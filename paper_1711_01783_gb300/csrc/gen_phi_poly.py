@@ -1,5 +1,14 @@
 """Generate phi_poly.h: polynomial pieces of the float phi(x) = -ln tanh(x/2).
 
+Two unit systems are fitted.  Natural units (LLRs in nats, used by the
+weighted-BP kernels) and base-2 units (LLRs in bits, y = x log2 e, used by the
+decoding kernels), where the map is psi(y) = log2(e) phi(y ln 2):
+
+  y <  Y0 :  psi(y) = C0 - lg2(y) - u * Qs(u),   u = y^2,  C0 = 1 - log2(ln 2)
+  y >= Y0 :  psi(y) = e * Ql(e^2),               e = 2^-y
+with Y0 = X0 log2 e.  In bits the hardware ex2 takes -y directly, which saves
+the multiplication by log2 e that the natural-unit large piece needs.
+
 Build-time script for the CUDA decoder (run by hand when the split point or
 degrees change; its output is committed).  The device evaluates phi on
 [phi(25), 25] as
@@ -22,7 +31,8 @@ import numpy as np
 X0 = 1.25
 # Two fits: "accurate" (used with float message storage; ~5e-8) and "half"
 # (used with half storage, whose rounding of 2^-11 dwarfs a ~3e-6 error).
-FITS = {"": (5, 4), "H": (3, 3)}   # prefix -> (coefficients of Ps, of Pl)
+FITS = {"": (5, 4)}                # natural units: prefix -> (coefficients of Ps, of Pl)
+FITS2 = {"2": (5, 4), "2H": (3, 3)}  # base-2 units: accurate and half
 
 
 def _cheb(lo, hi, k=6000):
@@ -43,6 +53,23 @@ def fit(deg_small, deg_large):
     return cs, cl, err_s, err_l
 
 
+def fit2(deg_small, deg_large):
+    """Base-2 pieces: Qs(u) = log2e h(sqrt(u) ln2) / u and Ql(z) = log2e 2 atanh(sqrt z)/sqrt z."""
+    ln2, log2e = np.log(2.0), 1.0 / np.log(2.0)
+    y0 = X0 * log2e
+    u = _cheb(1e-10, y0 * y0)
+    x = np.sqrt(u) * ln2
+    hs = log2e * np.log(np.tanh(x / 2) / (x / 2))
+    cs = np.polynomial.polynomial.polyfit(u, hs / u, deg_small - 1)
+    err_s = np.max(np.abs(np.polynomial.polynomial.polyval(u, cs) * u - hs))
+    z = _cheb(1e-14, np.exp(-2 * X0))
+    e = np.sqrt(z)
+    pl = log2e * 2.0 * np.arctanh(e) / e
+    cl = np.polynomial.polynomial.polyfit(z, pl, deg_large - 1)
+    err_l = np.max(np.abs(np.polynomial.polynomial.polyval(z, cl) / pl - 1))
+    return cs, cl, err_s, err_l
+
+
 def main():
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "phi_poly.h")
     lines = [
@@ -55,6 +82,18 @@ def main():
     for pre, (ds, dl) in FITS.items():
         cs, cl, err_s, err_l = fit(ds, dl)
         lines.append(f"// fit '{pre or 'accurate'}': max |small fit error| {err_s:.2e}, "
+                     f"max relative large fit error {err_l:.2e}")
+        for i, c in enumerate(cs):
+            lines.append(f"#define MLD_PHI{pre}_S{i} ({c:.9e}f)")
+        for i, c in enumerate(cl):
+            lines.append(f"#define MLD_PHI{pre}_L{i} ({c:.9e}f)")
+        print(pre, err_s, err_l)
+    ln2, log2e = np.log(2.0), 1.0 / np.log(2.0)
+    lines.append(f"#define MLD_PHI2_Y0 {X0 * log2e:.9g}f")
+    lines.append(f"#define MLD_PHI2_C0 {1.0 - np.log2(ln2):.9g}f")
+    for pre, (ds, dl) in FITS2.items():
+        cs, cl, err_s, err_l = fit2(ds, dl)
+        lines.append(f"// base-2 fit '{pre}': max |small fit error| {err_s:.2e} (bits), "
                      f"max relative large fit error {err_l:.2e}")
         for i, c in enumerate(cs):
             lines.append(f"#define MLD_PHI{pre}_S{i} ({c:.9e}f)")

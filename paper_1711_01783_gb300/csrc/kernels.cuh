@@ -26,10 +26,18 @@ constexpr int kBlock = 128;
 
 // ---------------------------------------------------------------------------
 // phi(x) = -ln tanh(x/2) in float, for x in [phi(lmax), lmax].
-// Two pieces (see gen_phi_poly.py): below MLD_PHI_X0, ln2 - ln x - t Ps(t)
-// with t = x^2; above, e Pl(e^2) with e = exp(-x).  ln and exp come from
-// the MUFU base-2 approximations.
+// Three fits (see gen_phi_poly.py):
+//   kFitNat : LLRs in nats (weighted BP): below MLD_PHI_X0, ln2 - ln x - t Ps(t)
+//             with t = x^2; above, e Pl(e^2) with e = exp(-x).
+//   kFitB2  : LLRs in bits, y = x log2 e (decoding, float storage): the same
+//             map psi(y) = log2(e) phi(y ln 2): below MLD_PHI2_Y0,
+//             C0 - lg2 y - u Qs(u) with u = y^2; above, e Ql(e^2), e = 2^-y.
+//   kFitB2H : as kFitB2 with shorter polynomials (half storage; error ~5e-6,
+//             far below half's 2^-11 rounding).
+// ln and exp come from the MUFU base-2 approximations.
 // ---------------------------------------------------------------------------
+enum Fit { kFitNat = 0, kFitB2 = 1, kFitB2H = 2 };
+
 __device__ __forceinline__ float mufu_lg2(float x) {
     float y;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -41,39 +49,49 @@ __device__ __forceinline__ float mufu_ex2(float x) {
     return y;
 }
 
-// Piece below MLD_PHI_X0.  HALF selects the shorter fit used with half
-// message storage (error ~3e-6, far below half's 2^-11 rounding).
-template <bool HALF>
+template <int F>
 __device__ __forceinline__ float phi_small(float x) {
-    const float kLn2 = 0.693147180559945309f;
     const float t = x * x;
     float ps;
-    if constexpr (HALF) {
-        ps = fmaf(MLD_PHIH_S2, t, MLD_PHIH_S1);
-        ps = fmaf(ps, t, MLD_PHIH_S0);
-    } else {
+    if constexpr (F == kFitNat) {
+        const float kLn2 = 0.693147180559945309f;
         ps = fmaf(MLD_PHI_S4, t, MLD_PHI_S3);
         ps = fmaf(ps, t, MLD_PHI_S2);
         ps = fmaf(ps, t, MLD_PHI_S1);
         ps = fmaf(ps, t, MLD_PHI_S0);
+        return fmaf(-t, ps, fmaf(-kLn2, mufu_lg2(x), kLn2));
+    } else {
+        if constexpr (F == kFitB2H) {
+            ps = fmaf(MLD_PHI2H_S2, t, MLD_PHI2H_S1);
+            ps = fmaf(ps, t, MLD_PHI2H_S0);
+        } else {
+            ps = fmaf(MLD_PHI2_S4, t, MLD_PHI2_S3);
+            ps = fmaf(ps, t, MLD_PHI2_S2);
+            ps = fmaf(ps, t, MLD_PHI2_S1);
+            ps = fmaf(ps, t, MLD_PHI2_S0);
+        }
+        return fmaf(-t, ps, MLD_PHI2_C0) - mufu_lg2(x);
     }
-    return fmaf(-t, ps, fmaf(-kLn2, mufu_lg2(x), kLn2));
 }
 
-// Piece at and above MLD_PHI_X0.
-template <bool HALF>
+template <int F>
 __device__ __forceinline__ float phi_large(float x) {
-    const float kLog2e = 1.442695040888963407f;
-    const float e = mufu_ex2(-kLog2e * x);
+    float e;
+    if constexpr (F == kFitNat) e = mufu_ex2(-1.442695040888963407f * x);
+    else e = mufu_ex2(-x);
     const float z = e * e;
     float pl;
-    if constexpr (HALF) {
-        pl = fmaf(MLD_PHIH_L2, z, MLD_PHIH_L1);
-        pl = fmaf(pl, z, MLD_PHIH_L0);
-    } else {
+    if constexpr (F == kFitNat) {
         pl = fmaf(MLD_PHI_L3, z, MLD_PHI_L2);
         pl = fmaf(pl, z, MLD_PHI_L1);
         pl = fmaf(pl, z, MLD_PHI_L0);
+    } else if constexpr (F == kFitB2H) {
+        pl = fmaf(MLD_PHI2H_L2, z, MLD_PHI2H_L1);
+        pl = fmaf(pl, z, MLD_PHI2H_L0);
+    } else {
+        pl = fmaf(MLD_PHI2_L3, z, MLD_PHI2_L2);
+        pl = fmaf(pl, z, MLD_PHI2_L1);
+        pl = fmaf(pl, z, MLD_PHI2_L0);
     }
     return e * pl;
 }
@@ -88,18 +106,20 @@ __device__ __forceinline__ float sel_lt(float x, float th, float a, float b) {
 
 // phi of one value: both pieces are evaluated and the right one selected
 // without branches, so the compiler can interleave independent chains.
-template <bool HALF>
+template <int F>
 __device__ __forceinline__ float phi_f(float x) {
-    return sel_lt(x, MLD_PHI_X0, phi_small<HALF>(x), phi_large<HALF>(x));
+    return sel_lt(x, F == kFitNat ? MLD_PHI_X0 : MLD_PHI2_Y0, phi_small<F>(x), phi_large<F>(x));
 }
 
-template <bool HALF>
+template <int F>
 __device__ __forceinline__ float4 phi4(float4 x) {
-    return make_float4(phi_f<HALF>(x.x), phi_f<HALF>(x.y), phi_f<HALF>(x.z), phi_f<HALF>(x.w));
+    return make_float4(phi_f<F>(x.x), phi_f<F>(x.y), phi_f<F>(x.z), phi_f<F>(x.w));
 }
 
 template <typename T> struct IsHalf { static constexpr bool value = false; };
 template <> struct IsHalf<__half> { static constexpr bool value = true; };
+// the fit the decoding kernels use for a message storage type
+template <typename T> struct DecodeFit { static constexpr int value = IsHalf<T>::value ? kFitB2H : kFitB2; };
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
     return fminf(fmaxf(x, lo), hi);
@@ -232,7 +252,7 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
     constexpr int NB = W / 8;
     constexpr int D = DC + DD;
     constexpr int dc = DC;
-    constexpr bool H = IsHalf<MsgT>::value;
+    constexpr int F = DecodeFit<MsgT>::value;
     const int32_t count = cl.count;
     int32_t j = static_cast<int32_t>(lt / TPC);
     const bool valid = j < count;
@@ -274,7 +294,7 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             // would; terms are only added, so no inf - inf arises
             const float4 m = make_float4(fminf(fabsf(q.x), lmax), fminf(fabsf(q.y), lmax),
                                          fminf(fabsf(q.z), lmax), fminf(fabsf(q.w), lmax));
-            const float4 ph = phi4<H>(m);
+            const float4 ph = phi4<F>(m);
 #pragma unroll
             for (int kk = 0; kk < kK; ++kk) {
                 const uint32_t qb = fbits(f4get(q, kk));
@@ -314,7 +334,7 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             float4 o = make_float4(fminf(pre[i][0] + suf[0], lmax), fminf(pre[i][1] + suf[1], lmax),
                                    fminf(pre[i][2] + suf[2], lmax), fminf(pre[i][3] + suf[3], lmax));
             if (D == 1) o = make_float4(amin, amin, amin, amin);
-            float4 m = phi4<H>(o);
+            float4 m = phi4<F>(o);
             if (D <= 2) m = make_float4(fminf(m.x, lmax), fminf(m.y, lmax), fminf(m.z, lmax), fminf(m.w, lmax));
             float4 rv;
 #pragma unroll
@@ -338,7 +358,7 @@ template <typename MsgT, int W>
 __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaunch &cl, int64_t lt, int slab) {
     constexpr int TPC = W / kK;
     constexpr int NB = W / 8;
-    constexpr bool H = IsHalf<MsgT>::value;
+    constexpr int F = DecodeFit<MsgT>::value;
     const int32_t j = static_cast<int32_t>(lt / TPC);
     if (j >= cl.count) return;
     const int lane0 = static_cast<int>(lt % TPC) * kK;
@@ -373,7 +393,7 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
         for (int kk = 0; kk < kK; ++kk) {
             const float qk = f4get(q, kk);
             par[kk] ^= fbits(qk);
-            S[kk] += phi_f<H>(clampf(fabsf(qk), amin, lmax));
+            S[kk] += phi_f<F>(clampf(fabsf(qk), amin, lmax));
         }
     }
     for (int i = 0; i < deg; ++i) {
@@ -384,8 +404,8 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
 #pragma unroll
         for (int kk = 0; kk < kK; ++kk) {
             const float qk = f4get(q, kk);
-            const float fk = phi_f<H>(clampf(fabsf(qk), amin, lmax));
-            const float mk = fminf(phi_f<H>(clampf(S[kk] - fk, amin, lmax)), lmax);
+            const float fk = phi_f<F>(clampf(fabsf(qk), amin, lmax));
+            const float mk = fminf(phi_f<F>(clampf(S[kk] - fk, amin, lmax)), lmax);
             f4set(rv, kk, bitsf(fbits(mk) | ((par[kk] ^ fbits(qk)) & kSign)));
         }
         if (out_core)
@@ -587,12 +607,14 @@ struct InArgs {
     const float *sigma;   // [B] or null (input is already an LLR)
     const int32_t *unit;
     int32_t n_vn, n_core, n_deg1, batch;
-    float lmax, amin;
+    float lmax;           // clamp of the channel LLR, nats
+    float scale;          // nats -> internal units (log2 e for decoding, 1 for weighted BP)
+    float lmax_i, amin_i; // phi argument clamps in internal units
     float *lch, *Lv, *lch1, *post1, *phi1;
 };
 
 // One tile of 32 natural VNs x W codewords of slab `slab`.
-template <int W, bool HALF>
+template <int W, int F>
 __device__ __forceinline__ void interleave_body(const InArgs &a, int tile_x, int slab) {
     __shared__ float tile[W][33];
     const int32_t j0 = tile_x * 32;
@@ -607,7 +629,7 @@ __device__ __forceinline__ void interleave_body(const InArgs &a, int tile_x, int
                 const float s = a.sigma[b];
                 v = (s > 0.f) ? v * (2.0f / (s * s)) : 0.f;
             }
-            v = clampf(v, -a.lmax, a.lmax) + 0.0f;  // -0 -> +0: a zero LLR has no sign
+            v = clampf(v, -a.lmax, a.lmax) * a.scale + 0.0f;  // -0 -> +0: a zero LLR has no sign
         }
         tile[w][jj] = v;
     }
@@ -628,15 +650,15 @@ __device__ __forceinline__ void interleave_body(const InArgs &a, int tile_x, int
             a.post1[o] = v;
             // the degree-1 VN's message never changes: its phi term, with the
             // sign of the LLR, is formed once here for every check update
-            const float f = phi_f<HALF>(clampf(fabsf(v), a.amin, a.lmax));
+            const float f = phi_f<F>(clampf(fabsf(v), a.amin_i, a.lmax_i));
             a.phi1[o] = bitsf(fbits(f) | (fbits(v) & kSign));
         }
     }
 }
 
-template <int W, bool HALF>
+template <int W, int F>
 __global__ void __launch_bounds__(kBlock) k_interleave_in(InArgs a) {
-    interleave_body<W, HALF>(a, blockIdx.x, blockIdx.y);
+    interleave_body<W, F>(a, blockIdx.x, blockIdx.y);
 }
 
 template <int W>
@@ -691,6 +713,7 @@ struct OutArgs {
     const float *Lv, *post1;
     uint8_t *bits;   // [B][n_vn]
     float *post;     // [B][n_vn] or null
+    float scale;     // internal units -> nats
 };
 
 template <int W>
@@ -716,7 +739,7 @@ __device__ __forceinline__ void deinterleave_body(const OutArgs &a, int tile_x, 
         if (b >= a.batch || j >= a.n_vn) continue;
         const float v = tile[jj][w];
         a.bits[static_cast<size_t>(b) * a.n_vn + j] = v < 0.f ? 1 : 0;
-        if (a.post) a.post[static_cast<size_t>(b) * a.n_vn + j] = v;
+        if (a.post) a.post[static_cast<size_t>(b) * a.n_vn + j] = v * a.scale;
     }
 }
 
@@ -725,10 +748,13 @@ __global__ void __launch_bounds__(kBlock) k_deinterleave_out(OutArgs a) {
     deinterleave_body<W>(a, blockIdx.x, blockIdx.y);
 }
 
-template <bool HALF>
-__global__ void k_phi_eval(const float *x, float *out, int64_t n, float lmax, float amin) {
+// phi of nats inputs through fit F: scale_in converts to the fit's units,
+// scale_out converts the result back to nats.
+template <int F>
+__global__ void k_phi_eval(const float *x, float *out, int64_t n, float scale_in, float lmax, float amin,
+                           float scale_out) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = fminf(phi_f<HALF>(clampf(x[i], amin, lmax)), lmax);
+    if (i < n) out[i] = fminf(phi_f<F>(clampf(x[i] * scale_in, amin, lmax)), lmax) * scale_out;
 }
 
 // ---------------------------------------------------------------------------
@@ -795,7 +821,9 @@ struct mld_decoder {
     int W = 32;
     int max_batch = 0;
     int max_slabs = 0;
-    float lmax = 25.f, amin = 0.f;
+    float lmax = 25.f, amin = 0.f;   // LLR clamp and phi(lmax), nats
+    // internal units of the decoding kernels (bits: an LLR times log2 e)
+    float lmax_i = 0.f, amin_i = 0.f, scale_in = 1.f, scale_out = 1.f;
     void *r = nullptr;
     float *Lv = nullptr, *lch = nullptr, *lch1 = nullptr, *post1 = nullptr, *phi1 = nullptr;
     uint8_t *hb_core = nullptr, *hb1 = nullptr, *sbits = nullptr;
@@ -814,6 +842,17 @@ struct mld_decoder {
 };
 
 namespace {
+
+// Sets the clamps and the nats <-> bits scales of a decoder from its lmax.
+inline void set_units(mld_decoder *d, float lmax) {
+    const double kLog2e = 1.4426950408889634074;
+    d->lmax = lmax;
+    d->amin = static_cast<float>(std::log1p(2.0 / std::expm1(static_cast<double>(lmax))));
+    d->lmax_i = static_cast<float>(lmax * kLog2e);
+    d->amin_i = static_cast<float>(std::log1p(2.0 / std::expm1(static_cast<double>(lmax))) * kLog2e);
+    d->scale_in = static_cast<float>(kLog2e);
+    d->scale_out = static_cast<float>(1.0 / kLog2e);
+}
 
 enum { kClsCheck = 0, kClsVar = 1, kClsSyn = 2, kClsLayout = 3 };
 

@@ -107,11 +107,11 @@ __global__ void __launch_bounds__(kBlock) km_lane(const JobDev *jobs, const Seg 
     if (t < j.slabs * DW) j.fail[(1 - parity) * j.slabs * DW + t] = 0u;
 }
 
-template <int W, bool HALF>
+template <int W, int F>
 __global__ void __launch_bounds__(kBlock) km_interleave(const JobDev *jobs, const Seg *segs, int nseg) {
     const Seg sg = segs[find_seg(segs, nseg)];
     const int local = blockIdx.x - sg.block0;
-    interleave_body<W, HALF>(jobs[sg.job].in, local % sg.bps, local / sg.bps);
+    interleave_body<W, F>(jobs[sg.job].in, local % sg.bps, local / sg.bps);
 }
 
 template <int W>
@@ -185,8 +185,8 @@ void launch_op_w(const mld_plan *p, const Op &op, cudaStream_t st) {
     const Seg *S = p->d_segs + op.seg0;
     switch (op.kind) {
         case kOpInterleave:
-            if (op.half) km_interleave<W, true><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg);
-            else km_interleave<W, false><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg);
+            if (op.half) km_interleave<W, kFitB2H><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg);
+            else km_interleave<W, kFitB2><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg);
             break;
         case kOpSynIn: km_syndrome_in<W><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg); break;
         case kOpHard:
@@ -248,15 +248,15 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
         JobDev x{};
         const bool y_mode = jb.sigma != nullptr;
         x.cn = CnArgs{d->g->cptr, d->g->col, d->g->dptr, h.n_cn, h.n_core, h.n_deg1, h.e_core, d->r, d->Lv,
-                      d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done, d->lmax, d->amin, 0, et ? 1 : 0};
+                      d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done, d->lmax_i, d->amin_i, 0, et ? 1 : 0};
         x.vn = VnArgs{d->g->vptr, d->g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0,
                       et ? 1 : 0};
         x.sy = SynArgs{d->g->cptr, d->g->col, d->g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core,
                        d->hb1, d->fail, d->done, et ? 1 : 0, jb.batch};
         x.in = InArgs{jb.in, y_mode ? jb.sigma : nullptr, d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch,
-                      d->lmax, d->amin, d->lch, d->Lv, d->lch1, d->post1, d->phi1};
+                      d->lmax, d->scale_in, d->lmax_i, d->amin_i, d->lch, d->Lv, d->lch1, d->post1, d->phi1};
         x.out = OutArgs{d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch, d->Lv, d->post1, jb.bits_out,
-                        jb.post_out};
+                        jb.post_out, d->scale_out};
         x.syn = jb.syndrome;
         x.cint = d->g->cint;
         x.sbits = d->sbits;

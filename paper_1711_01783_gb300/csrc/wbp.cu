@@ -70,7 +70,7 @@ struct CheckState {
             for (int k = 0; k < kK; ++k) {
                 x[i][k] = f4get(xv, k);
                 q[i][k] = clampf(wt[i] * x[i][k], -a.lmax, a.lmax);
-                f[i][k] = phi_f<false>(clampf(fabsf(q[i][k]), a.amin, a.lmax));
+                f[i][k] = phi_f<kFitNat>(clampf(fabsf(q[i][k]), a.amin, a.lmax));
                 if (q[i][k] < 0.f) sg[k] = -sg[k];
             }
         }
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kBlock) kw_check_fwd(WArgs a, float *r, const 
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
                 const float o = clampf(s.pre[i][k] + suf[k], a.amin, a.lmax);
-                const float m = fminf(phi_f<false>(o), a.lmax);
+                const float m = fminf(phi_f<kFitNat>(o), a.lmax);
                 const float sgn = (s.q[i][k] < 0.f) ? -s.sg[k] : s.sg[k];  // sign of the other terms
                 f4set(rv, k, sgn * m);
             }
@@ -401,10 +401,11 @@ int wbp_forward_w(mld_decoder *d, const float *llr, const uint8_t *syn, int32_t 
     const int slabs = (batch + W - 1) / W;
     const size_t rsz = static_cast<size_t>(slabs) * h.e_core * W;
     if (rsz) MLD_CUDA(cudaMemsetAsync(d->r, 0, rsz * sizeof(float), st));
-    InArgs ia{llr, nullptr, d->g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->lmax, d->amin,
+    // weighted BP works in nats: no scaling on entry or exit
+    InArgs ia{llr, nullptr, d->g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->lmax, 1.f, d->lmax, d->amin,
               d->lch, d->Lv, d->lch1, d->post1, d->phi1};
     if (h.n_vn > 0) {
-        k_interleave_in<W, false><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(ia);
+        k_interleave_in<W, kFitNat><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(ia);
         MLD_LAUNCHED("k_interleave_in");
     }
     if (h.n_cn > 0) {
@@ -414,7 +415,7 @@ int wbp_forward_w(mld_decoder *d, const float *llr, const uint8_t *syn, int32_t 
     const WArgs wa = wargs(d, w, n_types);
     int s = forward_iters<W>(d, wa, static_cast<float *>(d->r), d->Lv, 0, T, T, slabs, st, tape, nullptr, nullptr);
     if (s != MLD_OK) return s;
-    OutArgs oa{d->g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, d->bits_stage, soft};
+    OutArgs oa{d->g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, d->bits_stage, soft, 1.f};
     if (h.n_vn > 0) {
         k_deinterleave_out<W><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(oa);
         MLD_LAUNCHED("k_deinterleave_out");
