@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--train-steps", type=int, default=60)
+    ap.add_argument("--train-steps", type=int, default=80)
     ap.add_argument("--workload", default="fixed", choices=["fixed", "uneven", "wbp"],
                     help="fixed: one code, fixed iterations (the headline); uneven: 96 codewords over "
                          "rates 0.1/0.05/0.02 and n in {2^16, 2^18, 10^6}, caps 100/150/200, early "
@@ -312,7 +312,7 @@ def run_wbp(a, world, rank, local):
     data = [batch(20_000 + i) for i in range(16)]
     val = batch(40_000)
     wt = torch.ones((T, 3), device=dev, requires_grad=True)
-    opt = torch.optim.Adam([wt], lr=0.01)
+    opt = torch.optim.Adam([wt], lr=0.003)
     losses = []
 
     def val_loss():
@@ -363,7 +363,7 @@ def run_wbp(a, world, rank, local):
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MET ensemble, BIAWGN samples)",
         "config": {"workload": f"rate 0.1, n={n_tr}, {B_tr} codewords, T={T}, checkpoint every {k}, "
-                               f"20x3 weights, Adam lr 0.01, beta={beta}; judged at n={n_ev}, {B_ev} codewords"},
+                               f"20x3 weights, Adam lr 0.003, beta={beta}; judged at n={n_ev}, {B_ev} codewords"},
         "val_loss_unit_weights": val_before, "val_loss_trained": val_after,
         "train_loss_first5": float(np.mean(losses[:5])), "train_loss_last5": float(np.mean(losses[-5:])),
         "fer_plain_T20": fer["plain"], "fer_weighted_T20": fer["weighted"],
