@@ -257,19 +257,24 @@ int mld_wbp_backward(mld_tape *t, const float *dsoft, float *dw, float *dllr, vo
 int mld_tape_destroy(mld_tape *t);
 
 /* ---- kernel timing (measurement hook) -------------------------------------
- * With timing enabled, every later decode call on d records a pair of CUDA
- * events on its stream around each kernel it launches.  mld_decoder_timing_read
- * waits for those events, returns the device time and launch count summed per
- * kernel class since the last read, and clears them.  Classes: check update
- * (Eqs. 2-3), variable update (Eqs. 4-5), syndrome check (Step 5) and
- * layout kernels (interleave / de-interleave / bit packing).  Enabling adds
- * two event records per launch and changes no result.  Errors: MLD_EINVAL,
- * MLD_ECUDA. */
+ * mld_decoder_timing_enable(d, every): every = 0 turns timing off; every = N
+ * >= 1 makes later decode calls on d record a pair of CUDA events on their
+ * stream around the kernels of every N-th iteration (one pair around all
+ * check-update launches of that iteration, one around its variable update,
+ * one around its syndrome check) and around the entry and exit layout
+ * kernels.  mld_decoder_timing_read waits for those events and returns, per
+ * kernel class since the last read: the summed device time of the timed
+ * regions (*_ms), their number (*_timed), and the number of kernels launched
+ * while timing was on (*_launches, sampled or not); then it clears them.
+ * Classes: check update (Eqs. 2-3), variable update (Eqs. 4-5), syndrome
+ * check (Step 5), layout (interleave / de-interleave / bit packing).
+ * Timing changes no result.  Errors: MLD_EINVAL, MLD_ECUDA. */
 typedef struct {
     double check_ms, var_ms, syndrome_ms, layout_ms;
     int64_t check_launches, var_launches, syndrome_launches, layout_launches;
+    int64_t check_timed, var_timed, syndrome_timed, layout_timed;
 } mld_timing;
-int mld_decoder_timing_enable(mld_decoder *d, int enable);
+int mld_decoder_timing_enable(mld_decoder *d, int every);
 int mld_decoder_timing_read(mld_decoder *d, mld_timing *out);
 
 /* ---- decoding without any device allocation ------------------------------

@@ -59,7 +59,9 @@ class Timing(ctypes.Structure):
     _fields_ = [("check_ms", ctypes.c_double), ("var_ms", ctypes.c_double),
                 ("syndrome_ms", ctypes.c_double), ("layout_ms", ctypes.c_double),
                 ("check_launches", ctypes.c_int64), ("var_launches", ctypes.c_int64),
-                ("syndrome_launches", ctypes.c_int64), ("layout_launches", ctypes.c_int64)]
+                ("syndrome_launches", ctypes.c_int64), ("layout_launches", ctypes.c_int64),
+                ("check_timed", ctypes.c_int64), ("var_timed", ctypes.c_int64),
+                ("syndrome_timed", ctypes.c_int64), ("layout_timed", ctypes.c_int64)]
 
 
 class Job(ctypes.Structure):
@@ -302,9 +304,9 @@ class Decoder:
                                      _stream_handle(stream)))
         return soft, (Tape(h, self, llr.shape, (T, nt)) if keep_tape else None)
 
-    def timing(self, enable: bool):
-        """Record CUDA events around each kernel of later decode calls."""
-        _check(lib().mld_decoder_timing_enable(self._h, int(bool(enable))))
+    def timing(self, every: int):
+        """Time the kernels of every N-th iteration of later decode calls (0 = off)."""
+        _check(lib().mld_decoder_timing_enable(self._h, int(every)))
 
     def read_timing(self) -> dict:
         """Per-kernel-class device time (ms) and launch counts since the last read."""

@@ -88,6 +88,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     if (rbytes) MLD_CUDA(cudaMemsetAsync(d->r, 0, rbytes, st));
     MLD_CUDA(cudaMemsetAsync(d->done, 0, sizeof(uint32_t) * slabs * DW, st));
 
+    d->sample_now = true;
     InArgs ia{in, sigma, g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->lmax, d->scale_in, d->lmax_i, d->amin_i,
               d->lch, d->Lv, d->lch1, d->post1, d->phi1};
     if (h.n_vn > 0) {
@@ -157,9 +158,11 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     for (int32_t l = 1; l <= iters; ++l) {
         const bool last = (l == iters);
         ca.final_pass = (last || et) ? 1 : 0;
-        for (const ClassLaunch &cl : launches) {
-            int s = timed_launch(d, kClsCheck, st, "k_check_update",
-                                 [&] { launch_check_class<MsgT, W>(ca, cl, slabs, st); });
+        d->sample_now = ((l - 1) % d->timing_every) == 0;
+        {
+            int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
+                for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st);
+            }, static_cast<int>(launches.size()));
             if (s != MLD_OK) return s;
         }
         va.want_bits = (last || et) ? 1 : 0;
@@ -175,6 +178,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         }
     }
 
+    d->sample_now = true;
     OutArgs oa{g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, bits, post, d->scale_out};
     if (h.n_vn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_deinterleave_out", [&] {
@@ -418,7 +422,9 @@ int mld_decode_status(mld_decoder *d) {
 int mld_decoder_timing_enable(mld_decoder *d, int enable) {
     mld::clear_error();
     if (!d) return mld::fail(MLD_EINVAL, "timing_enable: null decoder");
+    if (enable < 0) return mld::fail(MLD_EINVAL, "timing_enable: negative period");
     d->timing = enable != 0;
+    d->timing_every = enable > 0 ? enable : 1;
     return MLD_OK;
 }
 
@@ -433,15 +439,20 @@ int mld_decoder_timing_read(mld_decoder *d, mld_timing *out) {
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.a, t.b);
         if (e != cudaSuccess && status == MLD_OK) status = cuda_fail(e, "timing_read");
         switch (t.cls) {
-            case kClsCheck: out->check_ms += ms; out->check_launches++; break;
-            case kClsVar: out->var_ms += ms; out->var_launches++; break;
-            case kClsSyn: out->syndrome_ms += ms; out->syndrome_launches++; break;
-            default: out->layout_ms += ms; out->layout_launches++; break;
+            case kClsCheck: out->check_ms += ms; out->check_timed++; break;
+            case kClsVar: out->var_ms += ms; out->var_timed++; break;
+            case kClsSyn: out->syndrome_ms += ms; out->syndrome_timed++; break;
+            default: out->layout_ms += ms; out->layout_timed++; break;
         }
         d->event_pool.push_back(t.a);
         d->event_pool.push_back(t.b);
     }
     d->timed.clear();
+    out->check_launches = d->launches[kClsCheck];
+    out->var_launches = d->launches[kClsVar];
+    out->syndrome_launches = d->launches[kClsSyn];
+    out->layout_launches = d->launches[kClsLayout];
+    for (int64_t &n : d->launches) n = 0;
     return status;
 }
 

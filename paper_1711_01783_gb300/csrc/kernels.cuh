@@ -837,6 +837,9 @@ struct mld_decoder {
     // kernel timing hook
     struct Timed { int cls; cudaEvent_t a, b; };
     bool timing = false;
+    int timing_every = 1;        // time every N-th iteration's launches
+    bool sample_now = true;      // the launches being enqueued are timed
+    int64_t launches[4] = {0, 0, 0, 0};  // kernels launched while timing is on, per class
     std::vector<Timed> timed;
     std::vector<cudaEvent_t> event_pool;
 };
@@ -867,11 +870,14 @@ cudaEvent_t pool_event(mld_decoder *d) {
     return e;
 }
 
-// Launch one kernel through `fn`, bracketed by timing events when enabled.
+// Launch `nk` kernels through `fn`, bracketed by one pair of timing events
+// when timing is on and this launch is sampled.
 template <typename F>
-int timed_launch(mld_decoder *d, int cls, cudaStream_t st, const char *what, F &&fn) {
+int timed_launch(mld_decoder *d, int cls, cudaStream_t st, const char *what, F &&fn, int nk = 1) {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (d->timing) {
+    if (d->timing) d->launches[cls] += nk;
+    const bool sample = d->timing && d->sample_now;
+    if (sample) {
         a = pool_event(d);
         b = pool_event(d);
         if (!a || !b) return mld::fail(MLD_ECUDA, "cudaEventCreate");
@@ -879,7 +885,7 @@ int timed_launch(mld_decoder *d, int cls, cudaStream_t st, const char *what, F &
     }
     fn();
     MLD_LAUNCHED(what);
-    if (d->timing) {
+    if (sample) {
         MLD_CUDA(cudaEventRecord(b, st));
         d->timed.push_back({cls, a, b});
     }

@@ -302,3 +302,29 @@ def test_full_size_sampled_codewords(mld, full_size, msg):
     assert np.array_equal(conv[sample], ref["converged"].astype(bool))
     d = np.abs(_np(out["post"])[sample].astype(np.float64) - ref["post"])
     print(f"{msg}: sampled posterior |dL| median {np.median(d):.3g} p99.9 {np.quantile(d, 0.999):.3g}")
+
+
+def test_sampled_timing_counts_and_changes_no_result(mld):
+    w = make_workload(0.1, 4096, 8, 1, 900, beta=0.4)
+    g = mld.Graph.from_edges(w.graph)
+    dec = mld.Decoder(g, 8, msg_dtype="f16")
+    L = _dev(_llr32(w))
+    s = _dev(w.s)
+    plain = dec.decode(L, s, iters=10, want_post=True)
+    dec.timing(3)
+    dec.read_timing()
+    timed = dec.decode(L, s, iters=10, want_post=True)
+    kt = dec.read_timing()
+    dec.timing(0)
+    assert np.array_equal(_np(plain["bits"]), _np(timed["bits"]))
+    assert np.array_equal(_np(plain["post"]), _np(timed["post"]))
+    # iterations 1, 4, 7 and 10 are timed; every launch is counted
+    assert kt["check_timed"] == 4 and kt["var_timed"] == 4
+    assert kt["var_launches"] == 10
+    assert kt["check_launches"] > 0 and kt["check_launches"] % 10 == 0
+    assert kt["check_ms"] > 0 and kt["var_ms"] > 0
+    assert kt["layout_timed"] == kt["layout_launches"] >= 2
+    assert kt["syndrome_launches"] == 2        # the final check and its lane update
+    assert dec.read_timing()["check_launches"] == 0
+    with pytest.raises(Exception):
+        dec.timing(-1)
