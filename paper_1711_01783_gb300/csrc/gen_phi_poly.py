@@ -7,7 +7,10 @@ decoding kernels), where the map is psi(y) = log2(e) phi(y ln 2):
   y <  Y0 :  psi(y) = C0 - lg2(y) - u * Qs(u),   u = y^2,  C0 = 1 - log2(ln 2)
   y >= Y0 :  psi(y) = e * Ql(e^2),               e = 2^-y
 with Y0 = X0 log2 e.  In bits the hardware ex2 takes -y directly, which saves
-the multiplication by log2 e that the natural-unit large piece needs.
+the multiplication by log2 e that the natural-unit large piece needs.  The
+device evaluates both base-2 pieces and takes their maximum: with a positive
+top coefficient of Qs the small piece drops below the large one past Y0, and
+the large piece stays below the small one under Y0 (check_max_of_pieces).
 
 Build-time script for the CUDA decoder (run by hand when the split point or
 degrees change; its output is committed).  The device evaluates phi on
@@ -29,10 +32,12 @@ import os
 import numpy as np
 
 X0 = 1.25
-# Two fits: "accurate" (used with float message storage; ~5e-8) and "half"
-# (used with half storage, whose rounding of 2^-11 dwarfs a ~3e-6 error).
+# Natural units: one fit (weighted BP).  Base-2 units: "accurate" (used with
+# float message storage; 1.5e-7 relative, about one float ulp) and "half"
+# (used with half storage: two coefficients per piece, 2.0e-4 relative,
+# below the 2^-11 = 4.9e-4 rounding of a stored message).
 FITS = {"": (5, 4)}                # natural units: prefix -> (coefficients of Ps, of Pl)
-FITS2 = {"2": (5, 4), "2H": (3, 3)}  # base-2 units: accurate and half
+FITS2 = {"2": (4, 4), "2H": (2, 2)}  # base-2 units: accurate and half
 
 
 def _cheb(lo, hi, k=6000):
@@ -70,6 +75,32 @@ def fit2(deg_small, deg_large):
     return cs, cl, err_s, err_l
 
 
+def check_max_of_pieces(cs, cl, lmax_nats=25.0):
+    """The device takes psi(y) = max(small piece, large piece).  Check, with
+    the coefficients rounded to float, that the maximum picks the accurate
+    piece everywhere on [psi(lmax), lmax]: past the split the small piece
+    must fall below the large one, which needs a positive top coefficient of
+    Qs.  Returns the maximum's largest relative error against psi."""
+    ln2 = np.log(2.0)
+    assert cs[-1] > 0, "top coefficient of Qs must be positive for the max() form"
+    ymax = lmax_nats / ln2
+    ymin = np.log1p(2.0 / np.expm1(lmax_nats)) / ln2
+    y = np.geomspace(ymin, ymax, 400001)
+    c32s = cs.astype(np.float32).astype(np.float64)
+    c32l = cl.astype(np.float32).astype(np.float64)
+    u = y * y
+    small = (1.0 - np.log2(ln2)) - u * np.polynomial.polynomial.polyval(u, c32s) - np.log2(y)
+    e = 2.0 ** -y
+    large = e * np.polynomial.polynomial.polyval(e * e, c32l)
+    ref = np.log1p(2.0 / np.expm1(y * ln2)) / ln2
+    got = np.maximum(small, large)
+    piece = np.where(y < X0 / ln2, small, large)
+    err_piece = np.max(np.abs(piece / ref - 1))
+    err = np.max(np.abs(got / ref - 1))
+    assert err <= 1.01 * err_piece + 1e-7, (err, err_piece)
+    return err
+
+
 def main():
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "phi_poly.h")
     lines = [
@@ -93,8 +124,10 @@ def main():
     lines.append(f"#define MLD_PHI2_C0 {1.0 - np.log2(ln2):.9g}f")
     for pre, (ds, dl) in FITS2.items():
         cs, cl, err_s, err_l = fit2(ds, dl)
+        err_max = check_max_of_pieces(cs, cl)
         lines.append(f"// base-2 fit '{pre}': max |small fit error| {err_s:.2e} (bits), "
-                     f"max relative large fit error {err_l:.2e}")
+                     f"max relative large fit error {err_l:.2e}; max(small, large) "
+                     f"relative error {err_max:.2e} on [psi(lmax), lmax]")
         for i, c in enumerate(cs):
             lines.append(f"#define MLD_PHI{pre}_S{i} ({c:.9e}f)")
         for i, c in enumerate(cl):

@@ -30,10 +30,11 @@ constexpr int kBlock = 128;
 //   kFitNat : LLRs in nats (weighted BP): below MLD_PHI_X0, ln2 - ln x - t Ps(t)
 //             with t = x^2; above, e Pl(e^2) with e = exp(-x).
 //   kFitB2  : LLRs in bits, y = x log2 e (decoding, float storage): the same
-//             map psi(y) = log2(e) phi(y ln 2): below MLD_PHI2_Y0,
-//             C0 - lg2 y - u Qs(u) with u = y^2; above, e Ql(e^2), e = 2^-y.
-//   kFitB2H : as kFitB2 with shorter polynomials (half storage; error ~5e-6,
-//             far below half's 2^-11 rounding).
+//             map psi(y) = log2(e) phi(y ln 2) as the larger of
+//             C0 - lg2 y - u Qs(u) (u = y^2; accurate below MLD_PHI2_Y0) and
+//             e Ql(e^2) (e = 2^-y; accurate above); error 1.5e-7 relative.
+//   kFitB2H : as kFitB2 with two coefficients per piece (half storage; error
+//             2.0e-4 relative, below half's 2^-11 rounding).
 // ln and exp come from the MUFU base-2 approximations.
 // ---------------------------------------------------------------------------
 enum Fit { kFitNat = 0, kFitB2 = 1, kFitB2H = 2 };
@@ -62,11 +63,9 @@ __device__ __forceinline__ float phi_small(float x) {
         return fmaf(-t, ps, fmaf(-kLn2, mufu_lg2(x), kLn2));
     } else {
         if constexpr (F == kFitB2H) {
-            ps = fmaf(MLD_PHI2H_S2, t, MLD_PHI2H_S1);
-            ps = fmaf(ps, t, MLD_PHI2H_S0);
+            ps = fmaf(MLD_PHI2H_S1, t, MLD_PHI2H_S0);
         } else {
-            ps = fmaf(MLD_PHI2_S4, t, MLD_PHI2_S3);
-            ps = fmaf(ps, t, MLD_PHI2_S2);
+            ps = fmaf(MLD_PHI2_S3, t, MLD_PHI2_S2);
             ps = fmaf(ps, t, MLD_PHI2_S1);
             ps = fmaf(ps, t, MLD_PHI2_S0);
         }
@@ -86,8 +85,7 @@ __device__ __forceinline__ float phi_large(float x) {
         pl = fmaf(pl, z, MLD_PHI_L1);
         pl = fmaf(pl, z, MLD_PHI_L0);
     } else if constexpr (F == kFitB2H) {
-        pl = fmaf(MLD_PHI2H_L2, z, MLD_PHI2H_L1);
-        pl = fmaf(pl, z, MLD_PHI2H_L0);
+        pl = fmaf(MLD_PHI2H_L1, z, MLD_PHI2H_L0);
     } else {
         pl = fmaf(MLD_PHI2_L3, z, MLD_PHI2_L2);
         pl = fmaf(pl, z, MLD_PHI2_L1);
@@ -104,11 +102,19 @@ __device__ __forceinline__ float sel_lt(float x, float th, float a, float b) {
     return r;
 }
 
-// phi of one value: both pieces are evaluated and the right one selected
-// without branches, so the compiler can interleave independent chains.
+// phi of one value: both pieces are evaluated without branches, so the
+// compiler can interleave independent chains.  In the base-2 fits the top
+// coefficient of Qs is positive, so past the split the small piece falls
+// below the large one (to -inf), and below the split the large piece stays
+// under the small one: their maximum is the right piece (near the split,
+// where both are accurate, whichever is larger).  One max replaces the
+// compare and select; gen_phi_poly.py checks the ordering on the whole range.
 template <int F>
 __device__ __forceinline__ float phi_f(float x) {
-    return sel_lt(x, F == kFitNat ? MLD_PHI_X0 : MLD_PHI2_Y0, phi_small<F>(x), phi_large<F>(x));
+    if constexpr (F == kFitNat)
+        return sel_lt(x, MLD_PHI_X0, phi_small<F>(x), phi_large<F>(x));
+    else
+        return fmaxf(phi_small<F>(x), phi_large<F>(x));
 }
 
 template <int F>

@@ -15,20 +15,17 @@
 #define MLD_PHI_L3 (3.259602744e-01f)
 #define MLD_PHI2_Y0 1.8033688f
 #define MLD_PHI2_C0 1.52876637f
-// base-2 fit '2': max |small fit error| 5.05e-09 (bits), max relative large fit error 4.63e-08
-#define MLD_PHI2_S0 (-5.776226393e-02f)
-#define MLD_PHI2_S1 (1.618846898e-03f)
-#define MLD_PHI2_S2 (-5.461420978e-05f)
-#define MLD_PHI2_S3 (1.962797304e-06f)
-#define MLD_PHI2_S4 (-5.779495718e-08f)
+// base-2 fit '2': max |small fit error| 1.59e-07 (bits), max relative large fit error 4.63e-08; max(small, large) relative error 1.46e-07 on [psi(lmax), lmax]
+#define MLD_PHI2_S0 (-5.776221345e-02f)
+#define MLD_PHI2_S1 (1.618349961e-03f)
+#define MLD_PHI2_S2 (-5.385014368e-05f)
+#define MLD_PHI2_S3 (1.586882831e-06f)
 #define MLD_PHI2_L0 (2.885389949e+00f)
 #define MLD_PHI2_L1 (9.618480019e-01f)
 #define MLD_PHI2_L2 (5.740022860e-01f)
 #define MLD_PHI2_L3 (4.702612714e-01f)
-// base-2 fit '2H': max |small fit error| 5.39e-06 (bits), max relative large fit error 2.78e-06
-#define MLD_PHI2H_S0 (-5.776050832e-02f)
-#define MLD_PHI2H_S1 (1.608909580e-03f)
-#define MLD_PHI2H_S2 (-4.610899829e-05f)
-#define MLD_PHI2H_L0 (2.885398074e+00f)
-#define MLD_PHI2H_L1 (9.600657329e-01f)
-#define MLD_PHI2H_L2 (6.319043797e-01f)
+// base-2 fit '2H': max |small fit error| 1.93e-04 (bits), max relative large fit error 1.82e-04; max(small, large) relative error 2.03e-04 on [psi(lmax), lmax]
+#define MLD_PHI2H_S0 (-5.769956003e-02f)
+#define MLD_PHI2H_S1 (1.458956707e-03f)
+#define MLD_PHI2H_L0 (2.884865946e+00f)
+#define MLD_PHI2H_L1 (1.011935603e+00f)

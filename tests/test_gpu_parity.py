@@ -9,8 +9,11 @@ Tolerances (derived from the arithmetic):
   roundings through phi and the prefix/suffix sums; a posterior sums up to
   d_v of them.  Bound used: |dL| <= 1e-4 + 1e-5 |L|.
 * One iteration, half messages: each stored message is rounded to half
-  (relative error <= 2^-11, |r| <= 25), so |dL| <= 2^-11 * sum_e |r_e| +
-  1e-4 <= 2^-11 * 25 * d_v + 1e-4.
+  (relative error <= 2^-11, |r| <= 25 nats) and carries the half fit's error:
+  2.3e-4 relative from the output phi, plus the inputs' 2.3e-4 relative error
+  in the leave-one-out sum y, which moves psi(y) by at most
+  max |y psi'(y)| * 2.3e-4 <= 1.45 * 2.3e-4 bits (2.3e-4 nats).  So
+  |dL| <= d_v * ((2^-11 + 2.3e-4) * 25 + 2.3e-4) + 1e-4.
 * After N iterations, float messages: hard decisions agree on >= 99.99 % of
   bits, converged flags and iteration counts identical, and every converged
   word satisfies H x = s exactly.
@@ -96,7 +99,7 @@ def test_library_reports_version(mld):
     assert "sm_103a" in mld.version()
 
 
-@pytest.mark.parametrize("msg,tol", [("f32", 2e-6), ("f16", 1e-5)])
+@pytest.mark.parametrize("msg,tol", [("f32", 2e-6), ("f16", 2.5e-4)])
 def test_phi_matches_closed_form(mld, msg, tol):
     lo = oracle.phi(25.0)
     x = np.exp(np.linspace(np.log(lo), np.log(25.0), 20001)).astype(np.float32)
@@ -120,7 +123,7 @@ def test_one_iteration_llr_error(mld, msg):
         bound = 1e-4 + 1e-5 * np.abs(ref["post"])
     else:
         dv = w.graph.vn_degree()[None, :]
-        bound = 2.0 ** -11 * 25.0 * dv + 1e-4
+        bound = dv * ((2.0 ** -11 + 2.3e-4) * 25.0 + 2.3e-4) + 1e-4
     assert np.all(d <= bound), (d.max(), (d - bound).max())
     print(f"{msg}: one-iteration |dL| max {d.max():.3g} mean {d.mean():.3g}")
 
