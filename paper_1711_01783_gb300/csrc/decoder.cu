@@ -72,6 +72,11 @@ void decoder_free(mld_decoder *d) {
     d->timed.clear();
     for (cudaEvent_t e : d->event_pool) cudaEventDestroy(e);
     d->event_pool.clear();
+    if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+    if (d->ev_join) cudaEventDestroy(d->ev_join);
+    if (d->side) cudaStreamDestroy(d->side);
+    d->ev_fork = d->ev_join = nullptr;
+    d->side = nullptr;
 }
 
 // Launch the full decode sequence on device buffers.
@@ -114,6 +119,15 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     // check-update launches, one per check class (built with the graph)
     const int wi = W == 8 ? 0 : (W == 16 ? 1 : (W == 32 ? 2 : 3));
     const std::vector<ClassLaunch> &launches = g->launches[wi];
+    // with a side stream and several classes, the largest runs on `st`
+    int big = -1;
+    if (d->side && launches.size() > 1) {
+        big = 0;
+        for (size_t i = 1; i < launches.size(); ++i)
+            if (static_cast<int64_t>(launches[i].blocks) * launches[i].deg >
+                static_cast<int64_t>(launches[big].blocks) * launches[big].deg)
+                big = static_cast<int>(i);
+    }
     const dim3 vn_grid(grid_x(static_cast<int64_t>(h.n_core) * TPC), slabs);
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, d->device);
@@ -161,7 +175,20 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         d->sample_now = ((l - 1) % d->timing_every) == 0;
         {
             int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
-                for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st);
+                if (big < 0) {
+                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st);
+                    return;
+                }
+                // the largest class on the caller's stream; the others on the
+                // side stream, whose blocks fill the SMs as its last wave
+                // drains (errors of the event calls surface as the launch error)
+                cudaEventRecord(d->ev_fork, st);
+                cudaStreamWaitEvent(d->side, d->ev_fork, 0);
+                launch_check_class<MsgT, W>(ca, launches[big], slabs, st);
+                for (size_t i = 0; i < launches.size(); ++i)
+                    if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(ca, launches[i], slabs, d->side);
+                cudaEventRecord(d->ev_join, d->side);
+                cudaStreamWaitEvent(st, d->ev_join, 0);
             }, static_cast<int>(launches.size()));
             if (s != MLD_OK) return s;
         }
@@ -376,6 +403,12 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     if (s == MLD_OK) s = dalloc(&d->post_stage, nb);
     if (s == MLD_OK) s = dalloc(&d->syn_stage, static_cast<size_t>(d->max_batch) * h.n_cn);
     if (s == MLD_OK) s = dalloc(&d->bits_stage, nb);
+    if (s == MLD_OK) {
+        cudaError_t ce = cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming);
+        if (ce != cudaSuccess) s = cuda_fail(ce, "decoder_create: side stream");
+    }
     if (s == MLD_OK) {
         cudaError_t e2 = cudaMemset(d->status, 0, sizeof(int32_t));
         if (e2 != cudaSuccess) s = cuda_fail(e2, "cudaMemset");

@@ -840,6 +840,10 @@ struct mld_decoder {
     // staging buffers for host pointers
     float *in_stage = nullptr, *sigma_stage = nullptr, *post_stage = nullptr;
     uint8_t *syn_stage = nullptr, *bits_stage = nullptr;
+    // side stream for check classes run beside the largest one (null: all
+    // classes on the caller's stream), with its fork and join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // kernel timing hook
     struct Timed { int cls; cudaEvent_t a, b; };
     bool timing = false;
