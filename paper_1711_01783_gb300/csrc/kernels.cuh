@@ -117,6 +117,27 @@ __device__ __forceinline__ float phi_f(float x) {
         return fmaxf(phi_small<F>(x), phi_large<F>(x));
 }
 
+// Three-input max (sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// phi of four values with the result floored at `lo`, base-2 fits: the max
+// of the two pieces and the floor in one instruction per value.  With
+// lo = phi(lmax) this equals phi of the argument clamped above at lmax (phi
+// decreases), and an argument of +inf gives lo (the small piece is -inf,
+// the large one 0), so the clamp needs no instruction of its own.
+template <int F>
+__device__ __forceinline__ float4 phi4_floor(float4 x, float lo) {
+    static_assert(F == kFitB2 || F == kFitB2H, "phi4_floor: base-2 fits only");
+    return make_float4(max3f(phi_small<F>(x.x), phi_large<F>(x.x), lo),
+                       max3f(phi_small<F>(x.y), phi_large<F>(x.y), lo),
+                       max3f(phi_small<F>(x.z), phi_large<F>(x.z), lo),
+                       max3f(phi_small<F>(x.w), phi_large<F>(x.w), lo));
+}
+
 template <int F>
 __device__ __forceinline__ float4 phi4(float4 x) {
     return make_float4(phi_f<F>(x.x), phi_f<F>(x.y), phi_f<F>(x.z), phi_f<F>(x.w));
@@ -294,13 +315,13 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             const float4 lv = ldf4(lvb + static_cast<size_t>(vidx[i]) * W);
             const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
             const float4 q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
-            // |q| is clamped above only: an argument below phi(lmax) gives a
-            // phi term above lmax (up to +inf at 0), which clamps every other
-            // term's leave-one-out sum to lmax exactly as the clamped term
-            // would; terms are only added, so no inf - inf arises
-            const float4 m = make_float4(fminf(fabsf(q.x), lmax), fminf(fabsf(q.y), lmax),
-                                         fminf(fabsf(q.z), lmax), fminf(fabsf(q.w), lmax));
-            const float4 ph = phi4<F>(m);
+            // phi(|q|) floored at amin = phi(lmax) is phi of |q| clamped above at
+            // lmax.  |q| is not clamped below: an argument under phi(lmax)
+            // gives a term above lmax (up to +inf at 0), which floors every
+            // other term's output at amin exactly as the clamped term would;
+            // terms are only added, so no inf - inf arises
+            const float4 m = make_float4(fabsf(q.x), fabsf(q.y), fabsf(q.z), fabsf(q.w));
+            const float4 ph = phi4_floor<F>(m, amin);
 #pragma unroll
             for (int kk = 0; kk < kK; ++kk) {
                 const uint32_t qb = fbits(f4get(q, kk));
@@ -334,20 +355,26 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
 #pragma unroll
     for (int i = D - 1; i >= 0; --i) {
         if (i < dc || a.final_pass) {
-            // every other term contributes phi(|q|) >= phi(lmax) ~ amin, so for
-            // D >= 2 the sum is already >= amin (up to rounding) and for D >= 3
-            // phi of it stays below lmax; only the needed clamps are applied
-            float4 o = make_float4(fminf(pre[i][0] + suf[0], lmax), fminf(pre[i][1] + suf[1], lmax),
-                                   fminf(pre[i][2] + suf[2], lmax), fminf(pre[i][3] + suf[3], lmax));
+            // the output floored at amin is phi of the sum clamped above at
+            // lmax.  Every other term is >= amin, so for D >= 3 the sum is at
+            // least 2 amin and phi of it stays below lmax; for D <= 2 the
+            // output is also clamped above
+            float4 o = make_float4(pre[i][0] + suf[0], pre[i][1] + suf[1], pre[i][2] + suf[2], pre[i][3] + suf[3]);
             if (D == 1) o = make_float4(amin, amin, amin, amin);
-            float4 m = phi4<F>(o);
+            float4 m = phi4_floor<F>(o, amin);
             if (D <= 2) m = make_float4(fminf(m.x, lmax), fminf(m.y, lmax), fminf(m.z, lmax), fminf(m.w, lmax));
             float4 rv;
 #pragma unroll
             for (int kk = 0; kk < kK; ++kk)
                 f4set(rv, kk, bitsf(fbits(f4get(m, kk)) | ((par[kk] ^ fbits(f[i][kk])) & kSign)));
             if (i < dc) {
-                if (valid) store_r<MsgT, W>(a, rb + static_cast<size_t>(e0 + i) * W, rv, donenib);
+                if (valid) {
+                    MsgT *rp = rb + static_cast<size_t>(e0 + i) * W;
+                    if (a.et)
+                        store_r<MsgT, W>(a, rp, rv, donenib);
+                    else
+                        Msg<MsgT>::store(rp, rv);
+                }
             } else {
                 emit_deg1<MsgT, W>(a, slab, s0 + i - dc, lane0, rv, donenib, valid);
             }
