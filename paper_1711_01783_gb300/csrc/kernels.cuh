@@ -337,21 +337,17 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             }
         }
     }
-    // exclusive prefix sums of |f|
+    // exclusive prefix sums of |f| (pre[0], which would be 0, is not formed:
+    // no addition below has a zero operand)
     float pre[D][kK];
-    {
-        float acc[kK] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
+    for (int kk = 0; kk < kK; ++kk) {
+        if (D >= 2) pre[1][kk] = fabsf(f[0][kk]);
 #pragma unroll
-            for (int kk = 0; kk < kK; ++kk) {
-                pre[i][kk] = acc[kk];
-                acc[kk] += fabsf(f[i][kk]);
-            }
-        }
+        for (int i = 2; i < D; ++i) pre[i][kk] = pre[i - 1][kk] + fabsf(f[i - 1][kk]);
     }
     // pass 2 (backwards): leave-one-out sum = prefix + suffix
-    float suf[kK] = {0.f, 0.f, 0.f, 0.f};
+    float suf[kK];
 #pragma unroll
     for (int i = D - 1; i >= 0; --i) {
         if (i < dc || a.final_pass) {
@@ -359,8 +355,16 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             // lmax.  Every other term is >= amin, so for D >= 3 the sum is at
             // least 2 amin and phi of it stays below lmax; for D <= 2 the
             // output is also clamped above
-            float4 o = make_float4(pre[i][0] + suf[0], pre[i][1] + suf[1], pre[i][2] + suf[2], pre[i][3] + suf[3]);
-            if (D == 1) o = make_float4(amin, amin, amin, amin);
+            float4 o;
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) {
+                float v;
+                if (D == 1) v = amin;                      // no other term
+                else if (i == D - 1) v = pre[i][kk];       // no suffix
+                else if (i == 0) v = suf[kk];              // no prefix
+                else v = pre[i][kk] + suf[kk];
+                f4set(o, kk, v);
+            }
             float4 m = phi4_floor<F>(o, amin);
             if (D <= 2) m = make_float4(fminf(m.x, lmax), fminf(m.y, lmax), fminf(m.z, lmax), fminf(m.w, lmax));
             float4 rv;
@@ -379,8 +383,10 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
                 emit_deg1<MsgT, W>(a, slab, s0 + i - dc, lane0, rv, donenib, valid);
             }
         }
+        if (i > 0) {
 #pragma unroll
-        for (int kk = 0; kk < kK; ++kk) suf[kk] += fabsf(f[i][kk]);
+            for (int kk = 0; kk < kK; ++kk) suf[kk] = (i == D - 1) ? fabsf(f[i][kk]) : suf[kk] + fabsf(f[i][kk]);
+        }
     }
 }
 
