@@ -103,6 +103,34 @@ typedef struct {
 } mld_graph_stats;
 int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out);
 
+/* ---- synthetic code ensemble ----------------------------------------------
+ * The seeded multi-edge-type ensemble the decoder is benchmarked on, built on
+ * the host.  (The paper decodes PEG-built MET codes whose degree
+ * distributions come from an external reference, Results and Table 1; this
+ * family has their shape.)  n_c = round(core_frac n) core VNs with 2 (the
+ * first 40 %) or 3 type-1 edges to m1 = n_c - round(rate n) type-1 checks and
+ * d2 type-2 edges to m2 = n - n_c type-2 checks; m2 degree-1 VNs, one per
+ * type-2 check; m = m1 + m2 = n - round(rate n) checks (the rate relation of
+ * the Methods).  Check sockets of each edge type are dealt evenly, shuffled
+ * and paired with VN sockets; repeated pairs are re-paired; VN and check
+ * labels are shuffled.  Random numbers: xoshiro256** seeded by splitmix64
+ * from (seed, n, d2).  Deterministic in the arguments on every machine.
+ * mld_ensemble_size  : edges and checks of (rate, n, d2, core_frac).  Host only.
+ * mld_ensemble_edges : the edge list into caller host buffers of `capacity`
+ *                      entries (>= the edge count), sorted by (check, VN);
+ *                      edge_type (may be NULL): 0 = type-1, 1 = type-2 of a
+ *                      core VN, 2 = degree-1 VN.  Host only.
+ * mld_graph_generate : mld_ensemble_edges with core_frac 0.20 / 0.12 / 0.06
+ *                      for rate 0.1 / 0.05 / 0.02 (other rates: MLD_EINVAL),
+ *                      then mld_graph_create.
+ * Errors: MLD_EINVAL (arguments, degenerate sizes, capacity), MLD_EGRAPH
+ * (re-pairing did not settle), and those of mld_graph_create. */
+int mld_ensemble_size(double rate, int32_t n, int32_t d2, double core_frac,
+                      int64_t *n_edges, int32_t *n_cn);
+int mld_ensemble_edges(double rate, int32_t n, int32_t d2, double core_frac, uint64_t seed,
+                       int32_t *edge_vn, int32_t *edge_cn, uint8_t *edge_type, int64_t capacity);
+int mld_graph_generate(double rate, int32_t n, int32_t d2, uint64_t seed, mld_graph **out);
+
 /* ---- decoder --------------------------------------------------------------
  * mld_decoder_create: allocate the device state for decoding up to
  * opts->max_batch codewords of graph g at once.  The graph must outlive the

@@ -34,7 +34,8 @@ EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destr
            "mld_decode_y", "mld_decode_status", "mld_decoder_timing_enable",
            "mld_decoder_timing_read", "mld_decode_noalloc", "mld_plan_create", "mld_plan_launch",
            "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_wbp_forward", "mld_wbp_backward",
-           "mld_tape_destroy", "mld_phi_eval")
+           "mld_tape_destroy", "mld_phi_eval", "mld_ensemble_size", "mld_ensemble_edges",
+           "mld_graph_generate")
 
 
 class MldError(RuntimeError):
@@ -82,6 +83,11 @@ def _load() -> ctypes.CDLL:
         "mld_version": (ctypes.c_char_p, []),
         "mld_graph_create": (ctypes.c_int, [P, P, P, I64, I32, I32, ctypes.POINTER(P)]),
         "mld_graph_destroy": (ctypes.c_int, [P]),
+        "mld_ensemble_size": (ctypes.c_int, [ctypes.c_double, I32, I32, ctypes.c_double,
+                                             ctypes.POINTER(I64), ctypes.POINTER(I32)]),
+        "mld_ensemble_edges": (ctypes.c_int, [ctypes.c_double, I32, I32, ctypes.c_double, ctypes.c_uint64,
+                                              P, P, P, I64]),
+        "mld_graph_generate": (ctypes.c_int, [ctypes.c_double, I32, I32, ctypes.c_uint64, ctypes.POINTER(P)]),
         "mld_graph_stats_get": (ctypes.c_int, [P, ctypes.POINTER(GraphStats)]),
         "mld_decoder_create": (ctypes.c_int, [P, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
         "mld_decoder_destroy": (ctypes.c_int, [P]),
@@ -151,6 +157,27 @@ def _ptr(x):
     return ctypes.c_void_p(x.data_ptr())
 
 
+# core-VN fraction of the ensemble per code rate (mld_graph_generate's table)
+ENSEMBLE_CORE_FRAC = {0.1: 0.20, 0.05: 0.12, 0.02: 0.06}
+
+
+def ensemble_edges(rate: float, n: int, d2: int, seed: int, core_frac: float | None = None):
+    """The library's seeded MET ensemble on the host (mld_ensemble_edges).
+
+    Returns (edge_vn int32, edge_cn int32, edge_type uint8, n_cn); no GPU is
+    needed.  ``core_frac`` defaults to the rate's entry of ENSEMBLE_CORE_FRAC.
+    """
+    cf = ENSEMBLE_CORE_FRAC[rate] if core_frac is None else float(core_frac)
+    e, m = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().mld_ensemble_size(float(rate), int(n), int(d2), cf, ctypes.byref(e), ctypes.byref(m)))
+    ev = np.empty(e.value, np.int32)
+    ec = np.empty(e.value, np.int32)
+    et = np.empty(e.value, np.uint8)
+    _check(lib().mld_ensemble_edges(float(rate), int(n), int(d2), cf, int(seed), _ptr(ev), _ptr(ec), _ptr(et),
+                                    e.value))
+    return ev, ec, et, int(m.value)
+
+
 class Graph:
     """Tanner graph uploaded to the current CUDA device (mld_graph_create)."""
 
@@ -173,6 +200,21 @@ class Graph:
         _check(lib().mld_graph_stats_get(h, ctypes.byref(st)))
         self.stats = {f: getattr(st, f) for f, _ in GraphStats._fields_}
         self.n_vn, self.n_cn = int(n_vn), int(n_cn)
+
+    @classmethod
+    def generate(cls, rate: float, n: int, d2: int, seed: int):
+        """The library's ensemble graph for rate 0.1 / 0.05 / 0.02 (mld_graph_generate)."""
+        import hashlib
+        h = ctypes.c_void_p()
+        _check(lib().mld_graph_generate(float(rate), int(n), int(d2), int(seed), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self._h = h
+        st = GraphStats()
+        _check(lib().mld_graph_stats_get(h, ctypes.byref(st)))
+        self.stats = {f: getattr(st, f) for f, _ in GraphStats._fields_}
+        self.n_vn, self.n_cn = int(st.n_vn), int(st.n_cn)
+        self.signature = hashlib.sha1(f"ensemble {rate} {n} {d2} {seed}".encode()).hexdigest()[:16]
+        return self
 
     @classmethod
     def from_edges(cls, g):
@@ -457,5 +499,6 @@ def phi(x, msg_dtype: str = "f32", stream=None):
     return out
 
 
-__all__ = ["Graph", "Decoder", "Plan", "Tape", "weighted_bp", "phi", "decode_noalloc", "version", "lib", "MldError", "EXPORTS",
+__all__ = ["Graph", "Decoder", "Plan", "Tape", "weighted_bp", "phi", "decode_noalloc", "ensemble_edges",
+           "ENSEMBLE_CORE_FRAC", "version", "lib", "MldError", "EXPORTS",
            "LIB_PATH", "NOALLOC_SCRATCH_BYTES"]
