@@ -131,9 +131,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     const dim3 vn_grid(grid_x(static_cast<int64_t>(h.n_core) * TPC), slabs);
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, d->device);
-    const int64_t syn_threads = static_cast<int64_t>(h.n_cn) * (W / 8);
-    const int syn_blocks = static_cast<int>(std::max<int64_t>(1, grid_x(syn_threads)));
-    const dim3 syn_grid(syn_blocks, slabs);
+    const dim3 syn_grid(syndrome_blocks(h.n_cn, sm_count), slabs);
     const int lane_blocks = (batch + 127) / 128;
 
     auto syndrome_round = [&](int32_t l, bool et_mode) -> int {

@@ -564,43 +564,76 @@ struct SynArgs {
     int32_t batch;         // codewords in the batch (later lanes are padding)
 };
 
-// Threads first, first + stride, ... of the (check, byte) index space of one
-// slab; every thread of the warp must call it (warp reduction at the end).
+// One slab's W decision bits of a node as one unsigned word.
+template <int W> struct SlabWord;
+template <> struct SlabWord<8> { using T = uint8_t; };
+template <> struct SlabWord<16> { using T = uint16_t; };
+template <> struct SlabWord<32> { using T = uint32_t; };
+template <> struct SlabWord<64> { using T = unsigned long long; };
+
+// Checks first, first + stride, ... of one slab, all W codewords of a check
+// in one word: x = syndrome row XOR the decision rows of the check's VNs
+// (gathered four at a time).  Every thread of the warp must call it (warp
+// reduction at the end).
 template <int W>
 __device__ __forceinline__ void syndrome_body(const SynArgs &a, int64_t first, int64_t stride, int slab) {
-    constexpr int NB = W / 8;
+    using T = typename SlabWord<W>::T;
     constexpr int DW = (W + 31) / 32;
-    const int g = threadIdx.x % NB;
-    const size_t cbase = static_cast<size_t>(slab) * a.n_cn;
-    const uint8_t *hc = a.hb_core + static_cast<size_t>(slab) * a.n_core * NB + g;
-    const uint8_t *h1 = a.hb1 + static_cast<size_t>(slab) * a.n_deg1 * NB + g;
-    uint32_t *fw = a.fail + slab * DW + (g * 8) / 32;
-    const int sh = (g * 8) & 31;
+    constexpr unsigned long long kFull = W == 64 ? ~0ull : ((1ull << W) - 1ull);
+    const T *hc = reinterpret_cast<const T *>(a.hb_core) + static_cast<size_t>(slab) * a.n_core;
+    const T *h1 = reinterpret_cast<const T *>(a.hb1) + static_cast<size_t>(slab) * a.n_deg1;
+    const T *sr = reinterpret_cast<const T *>(a.sbits) + static_cast<size_t>(slab) * a.n_cn;
     // codewords whose outcome is already known: frozen (early termination)
     // or padding lanes past the end of the batch
-    uint32_t known = a.et ? ((a.done[slab * DW + (g * 8) / 32] >> sh) & 0xFFu) : 0u;
-    const int first_lane = slab * W + g * 8;
-    if (first_lane + 8 > a.batch)
-        known |= (0xFFu << max(0, min(8, a.batch - first_lane))) & 0xFFu;
-    uint32_t acc = 0;
-    const int64_t total = static_cast<int64_t>(a.n_cn) * NB;
-    for (int64_t t = first; t < total; t += stride) {
-        // once each of this byte's 8 codewords has failed a check (or is
-        // frozen), further checks cannot change the result
-        if ((acc | known) == 0xFFu) break;
-        const int32_t c = static_cast<int32_t>(t / NB);
-        uint32_t x = a.sbits[(cbase + c) * NB + g];
-        for (int32_t e = a.cptr[c]; e < a.cptr[c + 1]; ++e) x ^= hc[static_cast<size_t>(__ldg(a.col + e)) * NB];
-        for (int32_t s = a.dptr[c]; s < a.dptr[c + 1]; ++s) x ^= h1[static_cast<size_t>(s) * NB];
+    unsigned long long known = 0;
+    if (a.et) {
+        known = a.done[slab * DW];
+        if (DW > 1) known |= static_cast<unsigned long long>(a.done[slab * DW + 1]) << 32;
+    }
+    const int valid = a.batch - slab * W;
+    if (valid < W) known |= ~0ull << valid;
+    known &= kFull;
+    unsigned long long acc = 0;
+    for (int64_t t = first; t < a.n_cn; t += stride) {
+        // once every codeword has failed a check (or is known), further
+        // checks cannot change the result
+        if ((acc | known) == kFull) break;
+        const int32_t c = static_cast<int32_t>(t);
+        T x = sr[c];
+        int32_t e = __ldg(a.cptr + c);
+        const int32_t e1 = __ldg(a.cptr + c + 1);
+        for (; e + 4 <= e1; e += 4) {
+            const int32_t v0 = __ldg(a.col + e), v1 = __ldg(a.col + e + 1);
+            const int32_t v2 = __ldg(a.col + e + 2), v3 = __ldg(a.col + e + 3);
+            x ^= static_cast<T>(hc[v0] ^ hc[v1] ^ hc[v2] ^ hc[v3]);
+        }
+        for (; e < e1; ++e) x ^= hc[__ldg(a.col + e)];
+        const int32_t s1 = __ldg(a.dptr + c + 1);
+        for (int32_t s = __ldg(a.dptr + c); s < s1; ++s) x ^= h1[s];
         acc |= x;
     }
     acc &= ~known;
+    uint32_t lo = static_cast<uint32_t>(acc), hi = static_cast<uint32_t>(acc >> 32);
 #pragma unroll
-    for (int o = 16; o >= NB; o >>= 1) acc |= __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    for (int o = 16; o >= 1; o >>= 1) {
+        lo |= __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        if (DW > 1) hi |= __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+    }
     // set only bits not already set: most warps of a failing slab then read
     // the word instead of contending on it
-    if ((threadIdx.x & 31) < NB && acc && ((*reinterpret_cast<volatile uint32_t *>(fw) >> sh) & acc) != acc)
-        atomicOr(fw, acc << sh);
+    if ((threadIdx.x & 31) == 0) {
+        uint32_t *fw = a.fail + slab * DW;
+        if (lo && (*reinterpret_cast<volatile uint32_t *>(fw) & lo) != lo) atomicOr(fw, lo);
+        if (DW > 1 && hi && (*reinterpret_cast<volatile uint32_t *>(fw + 1) & hi) != hi) atomicOr(fw + 1, hi);
+    }
+}
+
+// grid width (blocks per slab) of a syndrome check over n_cn checks: one
+// thread per check up to 8 blocks per SM, beyond that threads take several
+// checks (and can stop early once every codeword has failed)
+inline int syndrome_blocks(int64_t n_cn, int sm_count) {
+    const int64_t want = (n_cn + kBlock - 1) / kBlock;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(sm_count) * 8)));
 }
 
 template <int W>

@@ -238,6 +238,8 @@ void plan_free(mld_plan *p) {
 int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
                std::vector<JobDev> &jd, std::vector<Seg> &segs) {
     const bool et = (flags & MLD_EARLY_TERM) != 0;
+    int sm_count = 152;
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, p->device);
     int32_t lmax_iters = 0;
     for (int32_t j = 0; j < n_jobs; ++j) {
         const mld_job &jb = jobs[j];
@@ -341,8 +343,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
         const int parity = l & 1;
         for (int32_t j : js) {
             const mld_decoder *d = jobs[j].decoder;
-            const int64_t work = static_cast<int64_t>(jd[j].n_cn) * (d->W / 8);
-            const int bps = static_cast<int>(std::max<int64_t>(1, grid_x(work)));
+            const int bps = syndrome_blocks(jd[j].n_cn, sm_count);
             if (jd[j].n_cn > 0) groups[Key{kOpSyn, 0, d->W, 0, 0}].push_back(seg(j, bps, jd[j].slabs, 0));
         }
         flush(groups, l, parity);
