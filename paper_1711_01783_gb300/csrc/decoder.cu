@@ -132,6 +132,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     int sm_count = 152;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, d->device);
     const dim3 syn_grid(syndrome_blocks(h.n_cn, sm_count), slabs);
+    const int cap_blocks = sm_count * 16;  // two waves of 8 blocks per SM
     const int lane_blocks = (batch + 127) / 128;
 
     auto syndrome_round = [&](int32_t l, bool et_mode) -> int {
@@ -174,7 +175,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         {
             int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
                 if (big < 0) {
-                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st);
+                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st, cap_blocks);
                     return;
                 }
                 // the largest class on the caller's stream; the others on the
@@ -182,9 +183,9 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
                 // drains (errors of the event calls surface as the launch error)
                 cudaEventRecord(d->ev_fork, st);
                 cudaStreamWaitEvent(d->side, d->ev_fork, 0);
-                launch_check_class<MsgT, W>(ca, launches[big], slabs, st);
+                launch_check_class<MsgT, W>(ca, launches[big], slabs, st, cap_blocks);
                 for (size_t i = 0; i < launches.size(); ++i)
-                    if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(ca, launches[i], slabs, d->side);
+                    if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(ca, launches[i], slabs, d->side, cap_blocks);
                 cudaEventRecord(d->ev_join, d->side);
                 cudaStreamWaitEvent(st, d->ev_join, 0);
             }, static_cast<int>(launches.size()));

@@ -454,13 +454,28 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
     }
 }
 
+// Classes of at most 4 terms loop over their checks (a thread's set-up is a
+// large share of the work of a small check); larger ones take one check per
+// thread (the loop costs them registers).
+template <int D> constexpr bool kLoopedClass = D <= 4;
+
 // One check class per launch, its shape (DC, DD) a compile-time constant: the
 // register arrays are sized exactly and only this class's code is hot.
 template <typename MsgT, int W, int DC, int DD>
 __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
-    check_regular<MsgT, W, DC, DD>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, slab);
+    const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if constexpr (kLoopedClass<DC + DD>) {
+        // a capped grid; each thread takes every stride-th (check, lanes)
+        // pair, so its set-up is shared by several checks.  Both threads of
+        // a shuffle pair belong to one check and leave the loop together.
+        const int64_t total = static_cast<int64_t>(cl.count) * (W / kK);
+        const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+        for (int64_t lt = t0; lt < total; lt += stride) check_regular<MsgT, W, DC, DD>(a, cl, lt, slab);
+    } else {
+        check_regular<MsgT, W, DC, DD>(a, cl, t0, slab);
+    }
 }
 
 template <typename MsgT, int W>
@@ -473,12 +488,16 @@ __global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, Cla
 // Classes with at most one degree-1 VN per check and at most kMaxRegDeg terms
 // run the register kernel for their shape; any other class (possible in
 // caller graphs, not in the MET ensembles) runs the streaming kernel.
+// cap_blocks: grid width for the looped classes (a few waves of the GPU).
 template <typename MsgT, int W>
-void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st) {
+void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks) {
     const dim3 grid(cl.blocks, slabs);
+    const dim3 capped(std::max(1, std::min(cl.blocks, cap_blocks)), slabs);
     const int dd = cl.deg - cl.dc;
-#define MLD_CASE(DCV, DDV) \
-    case (DCV) * 2 + (DDV): k_check_update<MsgT, W, DCV, DDV><<<grid, kBlock, 0, st>>>(ca, cl); return;
+#define MLD_CASE(DCV, DDV)                                                                                   \
+    case (DCV) * 2 + (DDV):                                                                                  \
+        k_check_update<MsgT, W, DCV, DDV><<<kLoopedClass<(DCV) + (DDV)> ? capped : grid, kBlock, 0, st>>>(ca, cl); \
+        return;
     if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
         switch (cl.dc * 2 + dd) {
             MLD_CASE(1, 0) MLD_CASE(2, 0) MLD_CASE(3, 0) MLD_CASE(4, 0)
