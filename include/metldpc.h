@@ -83,7 +83,7 @@ const char *mld_version(void);
  * their posteriors are formed from the last check update (the "ignored VNs"
  * of Table 1 and the Discussion).  Errors: MLD_EINVAL for null/negative
  * arguments, MLD_EGRAPH for an out-of-range index, a repeated pair or more
- * than 2^31-1 edges, MLD_ENOMEM, MLD_ECUDA.  *out is set only on success. */
+ * than 2^30 edges, MLD_ENOMEM, MLD_ECUDA.  *out is set only on success. */
 #define MLD_MAX_EDGE_TYPES 8
 int mld_graph_create(const int32_t *edge_vn, const int32_t *edge_cn,
                      const uint8_t *edge_type, int64_t n_edges,

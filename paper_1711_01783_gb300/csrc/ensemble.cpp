@@ -94,7 +94,7 @@ int shape_of(double rate, int32_t n, int32_t d2, double core_frac, Shape *sh) {
     sh->e1 = 2 * sh->n_two + 3 * (sh->n_c - sh->n_two);
     sh->e2 = sh->n_c * static_cast<int64_t>(d2);
     sh->e3 = sh->m2;
-    if (sh->e1 + sh->e2 + sh->e3 > INT32_MAX) return mld::fail(MLD_EINVAL, "ensemble: more than 2^31-1 edges");
+    if (sh->e1 + sh->e2 + sh->e3 > (int64_t{1} << 30)) return mld::fail(MLD_EINVAL, "ensemble: more than 2^30 edges");
     return MLD_OK;
 }
 

@@ -32,8 +32,9 @@ int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
         return fail(MLD_EINVAL, "graph: negative size");
     if (n_edges > 0 && (!edge_vn || !edge_cn))
         return fail(MLD_EINVAL, "graph: null edge array");
-    if (n_edges > INT32_MAX)
-        return fail(MLD_EGRAPH, "graph: more than 2^31-1 edges");
+    // 2^30: 32-bit check and edge indices (and strided check loops) never overflow
+    if (n_edges > (int64_t{1} << 30))
+        return fail(MLD_EGRAPH, "graph: more than 2^30 edges");
     HostGraph &g = *out;
     g = HostGraph();
     g.n_vn = n_vn;

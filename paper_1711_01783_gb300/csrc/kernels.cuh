@@ -270,21 +270,20 @@ __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); 
 __device__ __forceinline__ float bitsf(uint32_t x) { return __uint_as_float(x); }
 constexpr uint32_t kSign = 0x80000000u;
 
-// Checks of one class: DC core edges and DD degree-1 VNs per check, all
-// terms in registers.  Threads past the class end work on its last check and
-// store nothing (so a whole shuffle pair stays active).
+// Check j of one class (DC core edges and DD degree-1 VNs per check, all
+// terms in registers), codewords lane0 .. lane0+3 of the slab.  A thread past
+// the class end works on its last check and stores nothing (so a whole
+// shuffle pair stays active).
 template <typename MsgT, int W, int DC, int DD>
-__device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch &cl, int64_t lt, int slab) {
-    constexpr int TPC = W / kK;
+__device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
+                                              int slab) {
     constexpr int NB = W / 8;
     constexpr int D = DC + DD;
     constexpr int dc = DC;
     constexpr int F = DecodeFit<MsgT>::value;
     const int32_t count = cl.count;
-    int32_t j = static_cast<int32_t>(lt / TPC);
     const bool valid = j < count;
     if (!valid) j = count - 1;
-    const int lane0 = static_cast<int>(lt % TPC) * kK;
     const int32_t c = cl.c0 + j;
     const int32_t e0 = cl.e0 + j * dc;
     const int32_t s0 = cl.s0 + j * (D - dc);
@@ -454,10 +453,10 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
     }
 }
 
-// Classes of at most 4 terms loop over their checks (a thread's set-up is a
-// large share of the work of a small check); larger ones take one check per
-// thread (the loop costs them registers).
-template <int D> constexpr bool kLoopedClass = D <= 4;
+// Classes of at most 6 terms loop over their checks on a capped grid: a
+// thread's set-up (indices, slab bases) is then shared by several checks.
+// The 7- and 8-term classes (80 registers) take one check per thread.
+template <int D> constexpr bool kLoopedClass = D <= 6;
 
 // One check class per launch, its shape (DC, DD) a compile-time constant: the
 // register arrays are sized exactly and only this class's code is hot.
@@ -465,16 +464,18 @@ template <typename MsgT, int W, int DC, int DD>
 __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
+    constexpr int TPC = W / kK;
     const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int lane0 = static_cast<int>(t0 % TPC) * kK;
     if constexpr (kLoopedClass<DC + DD>) {
-        // a capped grid; each thread takes every stride-th (check, lanes)
-        // pair, so its set-up is shared by several checks.  Both threads of
-        // a shuffle pair belong to one check and leave the loop together.
-        const int64_t total = static_cast<int64_t>(cl.count) * (W / kK);
-        const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-        for (int64_t lt = t0; lt < total; lt += stride) check_regular<MsgT, W, DC, DD>(a, cl, lt, slab);
+        // a capped grid; each thread takes every stride-th check with the
+        // same lanes, so its set-up is shared by several checks.  Both
+        // threads of a shuffle pair belong to one check and leave together.
+        const int32_t jstride = static_cast<int32_t>(gridDim.x) * (kBlock / TPC);
+        for (int32_t j = static_cast<int32_t>(t0 / TPC); j < cl.count; j += jstride)
+            check_regular<MsgT, W, DC, DD>(a, cl, j, lane0, slab);
     } else {
-        check_regular<MsgT, W, DC, DD>(a, cl, t0, slab);
+        check_regular<MsgT, W, DC, DD>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
     }
 }
 

@@ -54,14 +54,16 @@ __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6))
     const int local = blockIdx.x - sg.block0;
     const int slab = local / sg.bps;
     if (a.et && slab_all_done<W>(a.done, slab)) return;
+    constexpr int TPC = W / kK;
     const int64_t t0 = static_cast<int64_t>(local % sg.bps) * blockDim.x + threadIdx.x;
+    const int lane0 = static_cast<int>(t0 % TPC) * kK;
     if constexpr (kLoopedClass<DC + DD>) {
         // the segment's grid is capped (build_plan); threads loop over checks
-        const int64_t total = static_cast<int64_t>(sg.cl.count) * (W / kK);
-        const int64_t stride = static_cast<int64_t>(sg.bps) * blockDim.x;
-        for (int64_t lt = t0; lt < total; lt += stride) check_regular<MsgT, W, DC, DD>(a, sg.cl, lt, slab);
+        const int32_t jstride = sg.bps * (kBlock / TPC);
+        for (int32_t j = static_cast<int32_t>(t0 / TPC); j < sg.cl.count; j += jstride)
+            check_regular<MsgT, W, DC, DD>(a, sg.cl, j, lane0, slab);
     } else {
-        check_regular<MsgT, W, DC, DD>(a, sg.cl, t0, slab);
+        check_regular<MsgT, W, DC, DD>(a, sg.cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
     }
 }
 
@@ -401,8 +403,8 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
             for (const ClassLaunch &cl : d->g->launches[width_index(d->W)]) {
                 const int dd = cl.deg - cl.dc;
                 const bool regular = cl.dc >= 0 && (dd == 0 || dd == 1);
-                // looped register classes (at most 4 terms) run on a capped grid
-                const bool looped = regular && cl.deg <= 4;
+                // looped register classes (at most 6 terms) run on a capped grid
+                const bool looped = regular && cl.deg <= 6;
                 Seg s = seg(j, looped ? std::max(1, std::min(cl.blocks, sm_count * 16)) : cl.blocks, jd[j].slabs, fl);
                 s.cl = cl;
                 groups[Key{kOpCheck, half, d->W, regular ? cl.dc : -1, regular ? dd : -1}].push_back(s);
