@@ -18,7 +18,10 @@
  *    as `void *stream` (NULL = the legacy default stream).  Work is enqueued
  *    on that stream; the library never synchronizes the device.  With host
  *    buffers (no MLD_DEVICE_PTRS) the results are valid once that stream has
- *    been synchronized.
+ *    been synchronized, and the caller leaves the buffers untouched until
+ *    then: page-locked, mapped host buffers (cudaHostAlloc, cudaHostRegister,
+ *    torch pin_memory) are read and written in place by the kernels over the
+ *    host link; other host buffers are copied through the library's own.
  *  - Device: handles are bound to the CUDA device that was current when they
  *    were created; calls must be made with that device current.
  *  - LLRs follow L = ln p(x=0)/p(x=1); a bit is decided 1 iff its posterior
@@ -56,8 +59,9 @@ extern "C" {
                                  whose hard decision satisfies H x = s
                                  (Methods, Step 5)                             */
 #define MLD_DEVICE_PTRS 0x2u  /* all data pointers of the call are device
-                                 memory; otherwise they are host memory and the
-                                 library stages them through its own buffers  */
+                                 memory; otherwise they are host memory, used
+                                 in place when page-locked and mapped, else
+                                 staged through the library's own buffers     */
 
 typedef struct mld_graph mld_graph;
 typedef struct mld_decoder mld_decoder;

@@ -231,6 +231,18 @@ int dispatch_w(mld_decoder *d, const float *in, const float *sigma, const uint8_
     }
 }
 
+// The device address of a page-locked, mapped host buffer; null for any
+// other pointer (pageable memory is staged instead).
+const void *mapped_host(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // an unregistered pointer is not an error here
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int decode_common(mld_decoder *d, const float *in, const float *sigma, const uint8_t *syndrome,
                   int32_t batch, int32_t max_iters, uint32_t flags, uint8_t *bits_out,
                   float *post_out, uint8_t *converged, int32_t *iters_used, void *stream,
@@ -259,24 +271,47 @@ int decode_common(mld_decoder *d, const float *in, const float *sigma, const uin
     const uint8_t *dsyn = syndrome;
     uint8_t *dbits = bits_out;
     float *dpost = post_out;
+    // Host buffers that are page-locked and mapped into the device's address
+    // space (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory) are
+    // read and written by the layout kernels directly over the host link;
+    // other host buffers are staged through device copies.
+    const float *min = nullptr, *msig = nullptr;
+    const uint8_t *msyn = nullptr;
+    uint8_t *mbits = nullptr;
+    float *mpost = nullptr;
     if (!dev) {
-        if (nb) MLD_CUDA(cudaMemcpyAsync(d->in_stage, in, nb * sizeof(float), cudaMemcpyHostToDevice, st));
-        if (mb) MLD_CUDA(cudaMemcpyAsync(d->syn_stage, syndrome, mb, cudaMemcpyHostToDevice, st));
-        if (y_mode)
-            MLD_CUDA(cudaMemcpyAsync(d->sigma_stage, sigma, sizeof(float) * batch, cudaMemcpyHostToDevice, st));
-        din = d->in_stage;
-        dsyn = d->syn_stage;
-        dsig = y_mode ? d->sigma_stage : nullptr;
-        dbits = d->bits_stage;
-        dpost = post_out ? d->post_stage : nullptr;
+        min = static_cast<const float *>(mapped_host(in));
+        msyn = static_cast<const uint8_t *>(mapped_host(syndrome));
+        msig = y_mode ? static_cast<const float *>(mapped_host(sigma)) : nullptr;
+        mbits = static_cast<uint8_t *>(const_cast<void *>(mapped_host(bits_out)));
+        mpost = post_out ? static_cast<float *>(const_cast<void *>(mapped_host(post_out))) : nullptr;
+        if (min) din = min;
+        else {
+            if (nb) MLD_CUDA(cudaMemcpyAsync(d->in_stage, in, nb * sizeof(float), cudaMemcpyHostToDevice, st));
+            din = d->in_stage;
+        }
+        if (msyn) dsyn = msyn;
+        else {
+            if (mb) MLD_CUDA(cudaMemcpyAsync(d->syn_stage, syndrome, mb, cudaMemcpyHostToDevice, st));
+            dsyn = d->syn_stage;
+        }
+        if (y_mode) {
+            if (msig) dsig = msig;
+            else {
+                MLD_CUDA(cudaMemcpyAsync(d->sigma_stage, sigma, sizeof(float) * batch, cudaMemcpyHostToDevice, st));
+                dsig = d->sigma_stage;
+            }
+        }
+        dbits = mbits ? mbits : d->bits_stage;
+        dpost = post_out ? (mpost ? mpost : d->post_stage) : nullptr;
     }
     s = (d->msg == MLD_MSG_F16)
             ? dispatch_w<__half>(d, din, dsig, dsyn, batch, max_iters, et, dbits, dpost, converged, iters_used, st, dev)
             : dispatch_w<float>(d, din, dsig, dsyn, batch, max_iters, et, dbits, dpost, converged, iters_used, st, dev);
     if (s != MLD_OK) return s;
     if (!dev) {
-        if (nb) MLD_CUDA(cudaMemcpyAsync(bits_out, d->bits_stage, nb, cudaMemcpyDeviceToHost, st));
-        if (post_out && nb)
+        if (nb && !mbits) MLD_CUDA(cudaMemcpyAsync(bits_out, d->bits_stage, nb, cudaMemcpyDeviceToHost, st));
+        if (post_out && nb && !mpost)
             MLD_CUDA(cudaMemcpyAsync(post_out, d->post_stage, nb * sizeof(float), cudaMemcpyDeviceToHost, st));
     }
     return MLD_OK;
