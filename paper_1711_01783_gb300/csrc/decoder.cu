@@ -113,6 +113,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     CnArgs ca{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, h.e_core,
               d->r, d->Lv, d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done,
               d->lmax_i, d->amin_i, 0, et ? 1 : 0};
+    const bool hard1 = et && !post;  // degree-1 decisions only
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
                d->fail, d->done, et ? 1 : 0, batch};
@@ -175,7 +176,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         {
             int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
                 if (big < 0) {
-                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st, cap_blocks);
+                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st, cap_blocks, hard1);
                     return;
                 }
                 // the largest class on the caller's stream; the others on the
@@ -183,9 +184,9 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
                 // drains (errors of the event calls surface as the launch error)
                 cudaEventRecord(d->ev_fork, st);
                 cudaStreamWaitEvent(d->side, d->ev_fork, 0);
-                launch_check_class<MsgT, W>(ca, launches[big], slabs, st, cap_blocks);
+                launch_check_class<MsgT, W>(ca, launches[big], slabs, st, cap_blocks, hard1);
                 for (size_t i = 0; i < launches.size(); ++i)
-                    if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(ca, launches[i], slabs, d->side, cap_blocks);
+                    if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(ca, launches[i], slabs, d->side, cap_blocks, hard1);
                 cudaEventRecord(d->ev_join, d->side);
                 cudaStreamWaitEvent(st, d->ev_join, 0);
             }, static_cast<int>(launches.size()));
@@ -205,7 +206,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     }
 
     d->sample_now = true;
-    OutArgs oa{g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, bits, post, d->scale_out};
+    OutArgs oa{g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, d->hb1, bits, post, d->scale_out};
     if (h.n_vn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_deinterleave_out", [&] {
             k_deinterleave_out<W><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(oa);

@@ -252,6 +252,22 @@ __device__ __forceinline__ void emit_deg1(const CnArgs &a, int slab, int slot, i
     if (valid && (lane0 & 7) == 0) *hb = static_cast<uint8_t>(nib | (other << 4));
 }
 
+// Decisions of a degree-1 VN for 4 codewords (bit k: codeword lane0 + k) into
+// its bit-sliced byte; converged lanes keep the decision of their last
+// iteration.  Both threads of a shuffle pair must call it.
+template <int W>
+__device__ __forceinline__ void emit_deg1_bits(const CnArgs &a, int slab, int slot, int lane0, uint32_t nib,
+                                               uint32_t donenib, bool valid) {
+    constexpr int NB = W / 8;
+    uint8_t *hb = a.hb1 + (static_cast<size_t>(slab) * a.n_deg1 + slot) * NB + lane0 / 8;
+    if (donenib && valid) {
+        const uint32_t oldnib = (static_cast<uint32_t>(*hb) >> (lane0 & 7)) & 0xFu;
+        nib = (nib & ~donenib) | (oldnib & donenib);
+    }
+    const uint32_t other = __shfl_xor_sync(pair_mask(), nib, 1);
+    if (valid && (lane0 & 7) == 0) *hb = static_cast<uint8_t>(nib | (other << 4));
+}
+
 template <typename MsgT, int W>
 __device__ __forceinline__ void store_r(const CnArgs &a, MsgT *rp, float4 rv, uint32_t donenib) {
     if (donenib) {  // converged lanes keep their messages frozen
@@ -273,8 +289,9 @@ constexpr uint32_t kSign = 0x80000000u;
 // Check j of one class (DC core edges and DD degree-1 VNs per check, all
 // terms in registers), codewords lane0 .. lane0+3 of the slab.  A thread past
 // the class end works on its last check and stores nothing (so a whole
-// shuffle pair stays active).
-template <typename MsgT, int W, int DC, int DD>
+// shuffle pair stays active).  HARD1: a degree-1 VN gets its decision only,
+// not its posterior (early termination without soft output).
+template <typename MsgT, int W, int DC, int DD, bool HARD1 = false>
 __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
                                               int slab) {
     constexpr int NB = W / 8;
@@ -364,22 +381,40 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
                 else v = pre[i][kk] + suf[kk];
                 f4set(o, kk, v);
             }
-            float4 m = phi4_floor<F>(o, amin);
-            if (D <= 2) m = make_float4(fminf(m.x, lmax), fminf(m.y, lmax), fminf(m.z, lmax), fminf(m.w, lmax));
-            float4 rv;
+            if (HARD1 && i >= dc) {
+                // degree-1 VN, decisions only: the posterior L_ch + r is
+                // negative when both are, or when the negative one is the
+                // larger in magnitude; phi is a decreasing involution, so
+                // |r| = phi(o) > |L_ch| exactly when o < phi(|L_ch|) = |f|
+                uint32_t nib = 0;
 #pragma unroll
-            for (int kk = 0; kk < kK; ++kk)
-                f4set(rv, kk, bitsf(fbits(f4get(m, kk)) | ((par[kk] ^ fbits(f[i][kk])) & kSign)));
-            if (i < dc) {
-                if (valid) {
-                    MsgT *rp = rb + static_cast<size_t>(e0 + i) * W;
-                    if (a.et)
-                        store_r<MsgT, W>(a, rp, rv, donenib);
-                    else
-                        Msg<MsgT>::store(rp, rv);
+                for (int kk = 0; kk < kK; ++kk) {
+                    const uint32_t fb = fbits(f[i][kk]);
+                    const bool l_neg = (fb & kSign) != 0;
+                    const bool r_neg = ((par[kk] ^ fb) & kSign) != 0;
+                    const float fl = fabsf(f[i][kk]), ov = f4get(o, kk);
+                    const bool neg = (l_neg == r_neg) ? l_neg : (l_neg ? fl < ov : fl > ov);
+                    nib |= static_cast<uint32_t>(neg) << kk;
                 }
+                emit_deg1_bits<W>(a, slab, s0 + i - dc, lane0, nib, donenib, valid);
             } else {
-                emit_deg1<MsgT, W>(a, slab, s0 + i - dc, lane0, rv, donenib, valid);
+                float4 m = phi4_floor<F>(o, amin);
+                if (D <= 2) m = make_float4(fminf(m.x, lmax), fminf(m.y, lmax), fminf(m.z, lmax), fminf(m.w, lmax));
+                float4 rv;
+#pragma unroll
+                for (int kk = 0; kk < kK; ++kk)
+                    f4set(rv, kk, bitsf(fbits(f4get(m, kk)) | ((par[kk] ^ fbits(f[i][kk])) & kSign)));
+                if (i < dc) {
+                    if (valid) {
+                        MsgT *rp = rb + static_cast<size_t>(e0 + i) * W;
+                        if (a.et)
+                            store_r<MsgT, W>(a, rp, rv, donenib);
+                        else
+                            Msg<MsgT>::store(rp, rv);
+                    }
+                } else {
+                    emit_deg1<MsgT, W>(a, slab, s0 + i - dc, lane0, rv, donenib, valid);
+                }
             }
         }
         if (i > 0) {
@@ -460,7 +495,7 @@ template <int D> constexpr bool kLoopedClass = D <= 6;
 
 // One check class per launch, its shape (DC, DD) a compile-time constant: the
 // register arrays are sized exactly and only this class's code is hot.
-template <typename MsgT, int W, int DC, int DD>
+template <typename MsgT, int W, int DC, int DD, bool HARD1>
 __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
@@ -473,9 +508,9 @@ __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_update
         // threads of a shuffle pair belong to one check and leave together.
         const int32_t jstride = static_cast<int32_t>(gridDim.x) * (kBlock / TPC);
         for (int32_t j = static_cast<int32_t>(t0 / TPC); j < cl.count; j += jstride)
-            check_regular<MsgT, W, DC, DD>(a, cl, j, lane0, slab);
+            check_regular<MsgT, W, DC, DD, HARD1>(a, cl, j, lane0, slab);
     } else {
-        check_regular<MsgT, W, DC, DD>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
+        check_regular<MsgT, W, DC, DD, HARD1>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
     }
 }
 
@@ -489,15 +524,20 @@ __global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, Cla
 // Classes with at most one degree-1 VN per check and at most kMaxRegDeg terms
 // run the register kernel for their shape; any other class (possible in
 // caller graphs, not in the MET ensembles) runs the streaming kernel.
-// cap_blocks: grid width for the looped classes (a few waves of the GPU).
+// cap_blocks: grid width for the looped classes (a few waves of the GPU);
+// hard1: degree-1 decisions only (see check_regular).
 template <typename MsgT, int W>
-void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks) {
+void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks,
+                        bool hard1) {
     const dim3 grid(cl.blocks, slabs);
     const dim3 capped(std::max(1, std::min(cl.blocks, cap_blocks)), slabs);
+    const dim3 g = (cl.dc >= 0 && cl.deg <= 6) ? capped : grid;
     const int dd = cl.deg - cl.dc;
-#define MLD_CASE(DCV, DDV)                                                                                   \
-    case (DCV) * 2 + (DDV):                                                                                  \
-        k_check_update<MsgT, W, DCV, DDV><<<kLoopedClass<(DCV) + (DDV)> ? capped : grid, kBlock, 0, st>>>(ca, cl); \
+#define MLD_CASE(DCV, DDV)                                                                          \
+    case (DCV) * 2 + (DDV):                                                                         \
+        static_assert(kLoopedClass<(DCV) + (DDV)> == ((DCV) + (DDV) <= 6), "grid choice");         \
+        if (hard1) k_check_update<MsgT, W, DCV, DDV, (DDV) == 1><<<g, kBlock, 0, st>>>(ca, cl);   \
+        else k_check_update<MsgT, W, DCV, DDV, false><<<g, kBlock, 0, st>>>(ca, cl);              \
         return;
     if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
         switch (cl.dc * 2 + dd) {
@@ -803,6 +843,7 @@ struct OutArgs {
     const int32_t *unit;
     int32_t n_vn, n_core, n_deg1, batch;
     const float *Lv, *post1;
+    const uint8_t *hb1;  // degree-1 decisions (post1 is formed only for soft output)
     uint8_t *bits;   // [B][n_vn]
     float *post;     // [B][n_vn] or null
     float scale;     // internal units -> nats
@@ -810,18 +851,28 @@ struct OutArgs {
 
 template <int W>
 __device__ __forceinline__ void deinterleave_body(const OutArgs &a, int tile_x, int slab) {
+    constexpr int NB = W / 8;
     __shared__ float tile[32][W + 1];
+    __shared__ uint8_t tbit[32][W + 1];
     const int32_t j0 = tile_x * 32;
     for (int idx = threadIdx.x; idx < W * 32; idx += blockDim.x) {
         const int jj = idx / W, w = idx % W;
         const int32_t j = j0 + jj;
         float v = 0.f;
+        uint8_t bit = 0;
         if (j < a.n_vn) {
             const int32_t u = a.unit[j];
-            v = (u < a.n_core) ? a.Lv[(static_cast<size_t>(slab) * a.n_core + u) * W + w]
-                               : a.post1[(static_cast<size_t>(slab) * a.n_deg1 + (u - a.n_core)) * W + w];
+            if (u < a.n_core) {
+                v = a.Lv[(static_cast<size_t>(slab) * a.n_core + u) * W + w];
+                bit = v < 0.f ? 1 : 0;
+            } else {
+                const size_t s = static_cast<size_t>(slab) * a.n_deg1 + (u - a.n_core);
+                if (a.post) v = a.post1[s * W + w];
+                bit = (a.hb1[s * NB + w / 8] >> (w & 7)) & 1u;
+            }
         }
         tile[jj][w] = v;
+        tbit[jj][w] = bit;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < W * 32; idx += blockDim.x) {
@@ -829,9 +880,8 @@ __device__ __forceinline__ void deinterleave_body(const OutArgs &a, int tile_x, 
         const int b = slab * W + w;
         const int32_t j = j0 + jj;
         if (b >= a.batch || j >= a.n_vn) continue;
-        const float v = tile[jj][w];
-        a.bits[static_cast<size_t>(b) * a.n_vn + j] = v < 0.f ? 1 : 0;
-        if (a.post) a.post[static_cast<size_t>(b) * a.n_vn + j] = v * a.scale;
+        a.bits[static_cast<size_t>(b) * a.n_vn + j] = tbit[jj][w];
+        if (a.post) a.post[static_cast<size_t>(b) * a.n_vn + j] = tile[jj][w] * a.scale;
     }
 }
 

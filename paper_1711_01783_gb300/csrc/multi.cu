@@ -45,7 +45,7 @@ __device__ __forceinline__ int find_seg(const Seg *segs, int nseg) {
     return k;
 }
 
-template <typename MsgT, int W, int DC, int DD>
+template <typename MsgT, int W, int DC, int DD, bool HARD1>
 __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6))
     km_check(const JobDev *jobs, const Seg *segs, int nseg) {
     const Seg sg = segs[find_seg(segs, nseg)];
@@ -61,9 +61,9 @@ __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6))
         // the segment's grid is capped (build_plan); threads loop over checks
         const int32_t jstride = sg.bps * (kBlock / TPC);
         for (int32_t j = static_cast<int32_t>(t0 / TPC); j < sg.cl.count; j += jstride)
-            check_regular<MsgT, W, DC, DD>(a, sg.cl, j, lane0, slab);
+            check_regular<MsgT, W, DC, DD, HARD1>(a, sg.cl, j, lane0, slab);
     } else {
-        check_regular<MsgT, W, DC, DD>(a, sg.cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
+        check_regular<MsgT, W, DC, DD, HARD1>(a, sg.cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
     }
 }
 
@@ -145,6 +145,7 @@ enum OpKind { kOpMemset, kOpInterleave, kOpSynIn, kOpHard, kOpCheck, kOpVar, kOp
 
 struct Op {
     int kind = 0, half = 0, W = 0, dc = 0, dd = 0, parity = 0;
+    int hard1 = 0;  // check ops: degree-1 decisions only
     int32_t l = 0;
     int seg0 = 0, nseg = 0, blocks = 0;
     // memset / hard-decision ops
@@ -175,10 +176,11 @@ template <typename MsgT, int W>
 void launch_check_op(const mld_plan *p, const Op &op, cudaStream_t st) {
     const JobDev *J = p->d_jobs;
     const Seg *S = p->d_segs + op.seg0;
-#define MLD_CASE(DCV, DDV)                                                                  \
-    if (op.dc == (DCV) && op.dd == (DDV)) {                                                 \
-        km_check<MsgT, W, DCV, DDV><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg);          \
-        return;                                                                             \
+#define MLD_CASE(DCV, DDV)                                                                          \
+    if (op.dc == (DCV) && op.dd == (DDV)) {                                                         \
+        if (op.hard1) km_check<MsgT, W, DCV, DDV, (DDV) == 1><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg); \
+        else km_check<MsgT, W, DCV, DDV, false><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg);      \
+        return;                                                                                     \
     }
     MLD_CASE(1, 0) MLD_CASE(2, 0) MLD_CASE(3, 0) MLD_CASE(4, 0)
     MLD_CASE(5, 0) MLD_CASE(6, 0) MLD_CASE(7, 0) MLD_CASE(8, 0)
@@ -266,7 +268,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
                        d->hb1, d->fail, d->done, et ? 1 : 0, jb.batch};
         x.in = InArgs{jb.in, y_mode ? jb.sigma : nullptr, d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch,
                       d->lmax, d->scale_in, d->lmax_i, d->amin_i, d->lch, d->Lv, d->lch1, d->post1, d->phi1};
-        x.out = OutArgs{d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch, d->Lv, d->post1, jb.bits_out,
+        x.out = OutArgs{d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch, d->Lv, d->post1, d->hb1, jb.bits_out,
                         jb.post_out, d->scale_out};
         x.syn = jb.syndrome;
         x.cint = d->g->cint;
@@ -285,7 +287,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
     }
 
     // one op per group key; segments of the group are the jobs' shares
-    using Key = std::tuple<int, int, int, int, int>;  // kind, half, W, dc, dd
+    using Key = std::tuple<int, int, int, int, int, int>;  // kind, half, W, dc, dd, hard1
     auto flush = [&](std::map<Key, std::vector<Seg>> &groups, int32_t l, int parity) {
         for (auto &kv : groups) {
             Op op;
@@ -294,6 +296,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
             op.W = std::get<2>(kv.first);
             op.dc = std::get<3>(kv.first);
             op.dd = std::get<4>(kv.first);
+            op.hard1 = std::get<5>(kv.first);
             op.l = l;
             op.parity = parity;
             op.seg0 = static_cast<int>(segs.size());
@@ -342,9 +345,9 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
         const mld_decoder *d = jobs[j].decoder;
         const int half = d->msg == MLD_MSG_F16;
         if (jd[j].n_vn > 0)
-            groups[Key{kOpInterleave, half, d->W, 0, 0}].push_back(seg(j, (jd[j].n_vn + 31) / 32, jd[j].slabs, 0));
+            groups[Key{kOpInterleave, half, d->W, 0, 0, 0}].push_back(seg(j, (jd[j].n_vn + 31) / 32, jd[j].slabs, 0));
         if (jd[j].n_cn > 0)
-            groups[Key{kOpSynIn, 0, d->W, 0, 0}].push_back(seg(j, (jd[j].n_cn + 31) / 32, jd[j].slabs, 0));
+            groups[Key{kOpSynIn, 0, d->W, 0, 0, 0}].push_back(seg(j, (jd[j].n_cn + 31) / 32, jd[j].slabs, 0));
     }
     flush(groups, 0, 0);
 
@@ -353,13 +356,13 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
         for (int32_t j : js) {
             const mld_decoder *d = jobs[j].decoder;
             const int bps = syndrome_blocks(jd[j].n_cn, sm_count);
-            if (jd[j].n_cn > 0) groups[Key{kOpSyn, 0, d->W, 0, 0}].push_back(seg(j, bps, jd[j].slabs, 0));
+            if (jd[j].n_cn > 0) groups[Key{kOpSyn, 0, d->W, 0, 0, 0}].push_back(seg(j, bps, jd[j].slabs, 0));
         }
         flush(groups, l, parity);
         for (int32_t j : js) {
             const mld_decoder *d = jobs[j].decoder;
             const int lanes = std::max(jd[j].batch, jd[j].slabs * ((d->W + 31) / 32));
-            groups[Key{kOpLane, 0, d->W, 0, 0}].push_back(seg(j, (lanes + kBlock - 1) / kBlock, 1, 0));
+            groups[Key{kOpLane, 0, d->W, 0, 0, 0}].push_back(seg(j, (lanes + kBlock - 1) / kBlock, 1, 0));
         }
         flush(groups, l, parity);
     };
@@ -407,7 +410,8 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
                 const bool looped = regular && cl.deg <= 6;
                 Seg s = seg(j, looped ? std::max(1, std::min(cl.blocks, sm_count * 16)) : cl.blocks, jd[j].slabs, fl);
                 s.cl = cl;
-                groups[Key{kOpCheck, half, d->W, regular ? cl.dc : -1, regular ? dd : -1}].push_back(s);
+                const int hard1 = (et && !jobs[j].post_out && regular && dd == 1) ? 1 : 0;
+                groups[Key{kOpCheck, half, d->W, regular ? cl.dc : -1, regular ? dd : -1, hard1}].push_back(s);
             }
         }
         flush(groups, l, 0);
@@ -417,7 +421,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
             const int fl = (et || l == jobs[j].max_iters) ? 1 : 0;
             const int tpc = d->W / kK;
             const int bps = grid_x(static_cast<int64_t>(d->g->h.n_core) * tpc);
-            if (d->g->h.n_core > 0) groups[Key{kOpVar, half, d->W, 0, 0}].push_back(seg(j, bps, jd[j].slabs, fl));
+            if (d->g->h.n_core > 0) groups[Key{kOpVar, half, d->W, 0, 0, 0}].push_back(seg(j, bps, jd[j].slabs, fl));
             if (fl) checked.push_back(j);
         }
         flush(groups, l, 0);
@@ -426,7 +430,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
 
     for (int32_t j = 0; j < n_jobs; ++j)
         if (jd[j].n_vn > 0)
-            groups[Key{kOpOut, 0, jobs[j].decoder->W, 0, 0}].push_back(seg(j, (jd[j].n_vn + 31) / 32, jd[j].slabs, 0));
+            groups[Key{kOpOut, 0, jobs[j].decoder->W, 0, 0, 0}].push_back(seg(j, (jd[j].n_vn + 31) / 32, jd[j].slabs, 0));
     flush(groups, 0, 0);
     return MLD_OK;
 }
