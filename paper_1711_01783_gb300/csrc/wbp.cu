@@ -325,12 +325,25 @@ __global__ void __launch_bounds__(kBlock) kw_deinterleave(const float *core, con
     }
 }
 
-__global__ void kw_reduce_dw(const float *gwp, int blocks, int n_types, float *dw_row) {
-    const int k = threadIdx.x;
-    if (k >= n_types) return;
-    float v = 0.f;
-    for (int b = 0; b < blocks; ++b) v += gwp[static_cast<size_t>(b) * n_types + k];
-    dw_row[k] = v;
+// Sum over the per-block partials of each weight type in a fixed order
+// (strided over the threads, then a shared-memory tree), so the result does
+// not depend on scheduling.
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads) kw_reduce_dw(const float *gwp, int blocks, int n_types,
+                                                               float *dw_row) {
+    __shared__ float part[kReduceThreads];
+    for (int k = 0; k < n_types; ++k) {
+        float v = 0.f;
+        for (int b = threadIdx.x; b < blocks; b += kReduceThreads) v += gwp[static_cast<size_t>(b) * n_types + k];
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = kReduceThreads / 2; o > 0; o >>= 1) {
+            if (static_cast<int>(threadIdx.x) < o) part[threadIdx.x] += part[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) dw_row[k] = part[0];
+        __syncthreads();
+    }
 }
 
 }  // namespace
@@ -475,7 +488,7 @@ int wbp_backward_w(mld_tape *tp, const float *dsoft, float *dw, float *dllr, cud
                 kw_check_bwd<W><<<cgrid, kBlock, 0, st>>>(wa, rp, lvp, tp->gr, t == T ? tp->gd1 : nullptr, tp->gx,
                                                           tp->glch1, tp->gwp, t);
                 MLD_LAUNCHED("kw_check_bwd");
-                kw_reduce_dw<<<1, 32, 0, st>>>(tp->gwp, cgrid.x * cgrid.y, tp->n_types,
+                kw_reduce_dw<<<1, kReduceThreads, 0, st>>>(tp->gwp, cgrid.x * cgrid.y, tp->n_types,
                                                dw + static_cast<size_t>(t - 1) * tp->n_types);
                 MLD_LAUNCHED("kw_reduce_dw");
             } else {
