@@ -84,41 +84,94 @@ struct CheckState {
     }
 };
 
-// Forward check update of iteration t (messages updated in place; degree-1
-// posteriors written when `last`).
-template <int W>
+// Forward check update of iteration t for checks c0 .. c0+count-1 of at most
+// DMAX terms (messages updated in place; degree-1 posteriors written when
+// `last`).  The loops run to the compile-time DMAX with the check's degree
+// as a guard, so the per-term arrays stay in registers for small DMAX.
+template <int W, int DMAX>
 __global__ void __launch_bounds__(kBlock) kw_check_fwd(WArgs a, float *r, const float *lv, float *post1, int t,
-                                                       int last) {
+                                                       int last, int32_t c0, int32_t count) {
     constexpr int TPC = W / kK;
+    constexpr int NB = W / 8;
     const int slab = blockIdx.y;
     const int64_t lt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int32_t c = static_cast<int32_t>(lt / TPC);
-    if (c >= a.n_cn) return;
+    if (lt / TPC >= count) return;
+    const int32_t c = c0 + static_cast<int32_t>(lt / TPC);
     const int lane0 = static_cast<int>(lt % TPC) * kK;
-    CheckState<W> s;
-    s.load(a, c, slab, lane0, t, r, lv);
+    const int32_t e0 = a.cptr[c], nce = a.cptr[c + 1] - e0;
+    const int32_t s0 = a.dptr[c], deg = nce + (a.dptr[c + 1] - s0);
+    const uint32_t sb =
+        (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >> (lane0 & 7));
+    const float *wt_row = a.w + static_cast<size_t>(t - 1) * a.n_types;
+    float sg[kK], q[DMAX][kK], f[DMAX][kK], pre[DMAX][kK];
+#pragma unroll
+    for (int k = 0; k < kK; ++k) sg[k] = ((sb >> k) & 1u) ? -1.f : 1.f;
+    float acc[kK] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i) {
+        if (i < deg) {
+            float4 xv;
+            float wt;
+            if (i < nce) {
+                const int32_t e = e0 + i;
+                const float4 l = ldf4(lv + (static_cast<size_t>(slab) * a.n_core + a.col[e]) * W + lane0);
+                const float4 ro = ldf4(r + (static_cast<size_t>(slab) * a.e_core + e) * W + lane0);
+                xv = make_float4(l.x - ro.x, l.y - ro.y, l.z - ro.z, l.w - ro.w);
+                wt = wt_row[a.et_core[e]];
+            } else {
+                const int32_t sl = s0 + i - nce;
+                xv = ldf4(a.lch1 + (static_cast<size_t>(slab) * a.n_deg1 + sl) * W + lane0);
+                wt = wt_row[a.et_deg1[sl]];
+            }
+#pragma unroll
+            for (int k = 0; k < kK; ++k) {
+                q[i][k] = clampf(wt * f4get(xv, k), -a.lmax, a.lmax);
+                f[i][k] = phi_f<kFitNat>(clampf(fabsf(q[i][k]), a.amin, a.lmax));
+                if (q[i][k] < 0.f) sg[k] = -sg[k];
+                pre[i][k] = acc[k];
+                acc[k] += f[i][k];
+            }
+        }
+    }
     float suf[kK] = {0.f, 0.f, 0.f, 0.f};
-    for (int i = s.deg - 1; i >= 0; --i) {
-        const bool core = i < s.nce;
+#pragma unroll
+    for (int i = DMAX - 1; i >= 0; --i) {
+        if (i >= deg) continue;
+        const bool core = i < nce;
         if (core || last) {
             float4 rv;
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
-                const float o = clampf(s.pre[i][k] + suf[k], a.amin, a.lmax);
+                const float o = clampf(pre[i][k] + suf[k], a.amin, a.lmax);
                 const float m = fminf(phi_f<kFitNat>(o), a.lmax);
-                const float sgn = (s.q[i][k] < 0.f) ? -s.sg[k] : s.sg[k];  // sign of the other terms
+                const float sgn = (q[i][k] < 0.f) ? -sg[k] : sg[k];  // sign of the other terms
                 f4set(rv, k, sgn * m);
             }
             if (core) {
-                *reinterpret_cast<float4 *>(r + (static_cast<size_t>(slab) * a.e_core + s.e0 + i) * W + lane0) = rv;
+                *reinterpret_cast<float4 *>(r + (static_cast<size_t>(slab) * a.e_core + e0 + i) * W + lane0) = rv;
             } else {
-                const size_t o = (static_cast<size_t>(slab) * a.n_deg1 + s.s0 + i - s.nce) * W + lane0;
+                const size_t o = (static_cast<size_t>(slab) * a.n_deg1 + s0 + i - nce) * W + lane0;
                 const float4 l = ldf4(a.lch1 + o);
                 *reinterpret_cast<float4 *>(post1 + o) = make_float4(l.x + rv.x, l.y + rv.y, l.z + rv.z, l.w + rv.w);
             }
         }
 #pragma unroll
-        for (int k = 0; k < kK; ++k) suf[k] += s.f[i][k];
+        for (int k = 0; k < kK; ++k) suf[k] += f[i][k];
+    }
+}
+
+// Forward check update of one class: DMAX = the class's degree (at most
+// kMaxRegDeg), or kMaxTerms for the irregular class.
+template <int W>
+void launch_check_fwd(const WArgs &wa, const mld::ClassLaunch &cl, float *r, const float *lv, float *post1, int t,
+                      int last, int slabs, cudaStream_t st) {
+    const dim3 grid(cl.blocks, slabs);
+    switch (cl.deg) {
+#define MLD_FWD(DV) \
+        case DV: kw_check_fwd<W, DV><<<grid, kBlock, 0, st>>>(wa, r, lv, post1, t, last, cl.c0, cl.count); return;
+        MLD_FWD(1) MLD_FWD(2) MLD_FWD(3) MLD_FWD(4) MLD_FWD(5) MLD_FWD(6) MLD_FWD(7) MLD_FWD(8)
+#undef MLD_FWD
+        default: kw_check_fwd<W, kMaxTerms><<<grid, kBlock, 0, st>>>(wa, r, lv, post1, t, last, cl.c0, cl.count);
     }
 }
 
@@ -392,9 +445,8 @@ int forward_iters(mld_decoder *d, const WArgs &wa, float *r, float *lv, int t_be
             MLD_CUDA(cudaMemcpyAsync(seg_lv + (t - 1 - t_begin) * lsz, lv, lsz * sizeof(float),
                                      cudaMemcpyDeviceToDevice, st));
         }
-        if (h.n_cn > 0) {
-            kw_check_fwd<W><<<dim3(grid_x(static_cast<int64_t>(h.n_cn) * TPC), slabs), kBlock, 0, st>>>(
-                wa, r, lv, d->post1, t, t == T ? 1 : 0);
+        for (const mld::ClassLaunch &cl : d->g->launches[W == 8 ? 0 : (W == 16 ? 1 : (W == 32 ? 2 : 3))]) {
+            launch_check_fwd<W>(wa, cl, r, lv, d->post1, t, t == T ? 1 : 0, slabs, st);
             MLD_LAUNCHED("kw_check_fwd");
         }
         if (h.n_core > 0) {
