@@ -29,15 +29,17 @@ struct WArgs {
 
 __device__ __forceinline__ float inv_sinh(float x) { return 1.0f / sinhf(x); }
 
-// Recomputes the forward quantities of one check for 4 codewords at
-// iteration t from r^{t-1} (rp) and L_v^{t-1} (lvp).
-template <int W>
+// Recomputes the forward quantities of one check (at most DMAX terms) for 4
+// codewords at iteration t from r^{t-1} (rp) and L_v^{t-1} (lvp).  Loops run
+// to DMAX with the check's degree as a guard, so the arrays stay in
+// registers for small DMAX.
+template <int W, int DMAX>
 struct CheckState {
     int nce, deg;
     int32_t e0, s0;
-    float x[kMaxTerms][kK], q[kMaxTerms][kK], f[kMaxTerms][kK], pre[kMaxTerms][kK];
-    float wt[kMaxTerms];
-    int ty[kMaxTerms];
+    float x[DMAX][kK], q[DMAX][kK], f[DMAX][kK], pre[DMAX][kK];
+    float wt[DMAX];
+    int ty[DMAX];
     float sg[kK];  // product of signs and syndrome sign over all terms
 
     __device__ __forceinline__ void load(const WArgs &a, int c, int slab, int lane0, int t, const float *rp,
@@ -52,7 +54,10 @@ struct CheckState {
         const float *wt_row = a.w + static_cast<size_t>(t - 1) * a.n_types;
 #pragma unroll
         for (int k = 0; k < kK; ++k) sg[k] = ((sb >> k) & 1u) ? -1.f : 1.f;
-        for (int i = 0; i < deg; ++i) {
+        float acc[kK] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            if (i >= deg) continue;
             float4 xv;
             if (i < nce) {
                 const int32_t e = e0 + i;
@@ -72,15 +77,10 @@ struct CheckState {
                 q[i][k] = clampf(wt[i] * x[i][k], -a.lmax, a.lmax);
                 f[i][k] = phi_f<kFitNat>(clampf(fabsf(q[i][k]), a.amin, a.lmax));
                 if (q[i][k] < 0.f) sg[k] = -sg[k];
-            }
-        }
-        float acc[kK] = {0.f, 0.f, 0.f, 0.f};
-        for (int i = 0; i < deg; ++i)
-#pragma unroll
-            for (int k = 0; k < kK; ++k) {
                 pre[i][k] = acc[k];
                 acc[k] += f[i][k];
             }
+        }
     }
 };
 
@@ -181,25 +181,28 @@ void launch_check_fwd(const WArgs &wa, const mld::ClassLaunch &cl, float *r, con
 //   gx   : dloss/dx^t for core edges (written)
 //   glch1: dloss/dL_ch of degree-1 VNs (accumulated)
 //   gwp  : per-block partial dloss/dw[t][type] (written, [gridDim.x*gridDim.y][n_types])
-template <int W>
+template <int W, int DMAX>
 __global__ void __launch_bounds__(kBlock) kw_check_bwd(WArgs a, const float *rp, const float *lvp, const float *gr,
-                                                       const float *gd1, float *gx, float *glch1, float *gwp, int t) {
+                                                       const float *gd1, float *gx, float *glch1, float *gwp, int t,
+                                                       int32_t c0, int32_t count, int32_t part0) {
     constexpr int TPC = W / kK;
     __shared__ float red[kBlock / 32][kMaxTypes];
     const int slab = blockIdx.y;
     const int64_t lt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int32_t c = static_cast<int32_t>(lt / TPC);
     float gw[kMaxTypes];
 #pragma unroll
     for (int k = 0; k < kMaxTypes; ++k) gw[k] = 0.f;
-    if (c < a.n_cn) {
+    if (lt / TPC < count) {
+        const int32_t c = c0 + static_cast<int32_t>(lt / TPC);
         const int lane0 = static_cast<int>(lt % TPC) * kK;
-        CheckState<W> s;
+        CheckState<W, DMAX> s;
         s.load(a, c, slab, lane0, t, rp, lvp);
         // g_o_i = sign_i * g_r_i * phi'(o_i) where o_i is strictly inside the clamp
-        float go[kMaxTerms][kK];
+        float go[DMAX][kK];
         float suf[kK] = {0.f, 0.f, 0.f, 0.f};
-        for (int i = s.deg - 1; i >= 0; --i) {
+#pragma unroll
+        for (int i = DMAX - 1; i >= 0; --i) {
+            if (i >= s.deg) continue;
             const bool core = i < s.nce;
             float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
             if (core)
@@ -215,18 +218,23 @@ __global__ void __launch_bounds__(kBlock) kw_check_bwd(WArgs a, const float *rp,
             }
         }
         // g_f_j = sum_{i != j} g_o_i (prefix + suffix), then back through phi, |.|, clamp, weight
-        float gpre[kMaxTerms][kK];
+        float gpre[DMAX][kK];
         float acc[kK] = {0.f, 0.f, 0.f, 0.f};
-        for (int i = 0; i < s.deg; ++i)
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) {
+            if (i >= s.deg) continue;
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
                 gpre[i][k] = acc[k];
                 acc[k] += go[i][k];
             }
+        }
         float gsuf[kK] = {0.f, 0.f, 0.f, 0.f};
-        for (int i = s.deg - 1; i >= 0; --i) {
-            float4 gxv;
+#pragma unroll
+        for (int i = DMAX - 1; i >= 0; --i) {
+            if (i >= s.deg) continue;
             float gxd[kK];
+            float gwi = 0.f;  // this term's weight gradient over the 4 codewords
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
                 const float gf = gpre[i][k] + gsuf[k];
@@ -236,17 +244,19 @@ __global__ void __launch_bounds__(kBlock) kw_check_bwd(WArgs a, const float *rp,
                 const float gq = s.q[i][k] > 0.f ? ga : (s.q[i][k] < 0.f ? -ga : 0.f);
                 const float p = s.wt[i] * s.x[i][k];
                 const float gp = (p > -a.lmax && p < a.lmax) ? gq : 0.f;
-                gw[s.ty[i]] += gp * s.x[i][k];
+                gwi += gp * s.x[i][k];
                 gxd[k] = gp * s.wt[i];
             }
-            gxv = make_float4(gxd[0], gxd[1], gxd[2], gxd[3]);
+#pragma unroll
+            for (int k = 0; k < kMaxTypes; ++k) gw[k] += (k == s.ty[i]) ? gwi : 0.f;
+            const float4 gxv = make_float4(gxd[0], gxd[1], gxd[2], gxd[3]);
             if (i < s.nce) {
                 *reinterpret_cast<float4 *>(gx + (static_cast<size_t>(slab) * a.e_core + s.e0 + i) * W + lane0) = gxv;
             } else {
-                float *p = glch1 + (static_cast<size_t>(slab) * a.n_deg1 + s.s0 + i - s.nce) * W + lane0;
-                float4 o = *reinterpret_cast<float4 *>(p);
+                float *pp = glch1 + (static_cast<size_t>(slab) * a.n_deg1 + s.s0 + i - s.nce) * W + lane0;
+                float4 o = *reinterpret_cast<float4 *>(pp);
                 o.x += gxv.x; o.y += gxv.y; o.z += gxv.z; o.w += gxv.w;
-                *reinterpret_cast<float4 *>(p) = o;
+                *reinterpret_cast<float4 *>(pp) = o;
             }
         }
     }
@@ -261,7 +271,28 @@ __global__ void __launch_bounds__(kBlock) kw_check_bwd(WArgs a, const float *rp,
     if (threadIdx.x < a.n_types) {
         float v = 0.f;
         for (int i = 0; i < kBlock / 32; ++i) v += red[i][threadIdx.x];
-        gwp[(static_cast<size_t>(blockIdx.y) * gridDim.x + blockIdx.x) * a.n_types + threadIdx.x] = v;
+        gwp[(static_cast<size_t>(part0) + static_cast<size_t>(blockIdx.y) * gridDim.x + blockIdx.x) * a.n_types +
+            threadIdx.x] = v;
+    }
+}
+
+// Adjoint check update of one class; its block partials start at part0.
+template <int W>
+void launch_check_bwd(const WArgs &wa, const mld::ClassLaunch &cl, const float *rp, const float *lvp,
+                      const float *gr, const float *gd1, float *gx, float *glch1, float *gwp, int t, int slabs,
+                      int32_t part0, cudaStream_t st) {
+    const dim3 grid(cl.blocks, slabs);
+    switch (cl.deg) {
+#define MLD_BWD(DV)                                                                                         \
+        case DV:                                                                                            \
+            kw_check_bwd<W, DV><<<grid, kBlock, 0, st>>>(wa, rp, lvp, gr, gd1, gx, glch1, gwp, t, cl.c0,    \
+                                                         cl.count, part0);                                  \
+            return;
+        MLD_BWD(1) MLD_BWD(2) MLD_BWD(3) MLD_BWD(4) MLD_BWD(5) MLD_BWD(6) MLD_BWD(7) MLD_BWD(8)
+#undef MLD_BWD
+        default:
+            kw_check_bwd<W, kMaxTerms><<<grid, kBlock, 0, st>>>(wa, rp, lvp, gr, gd1, gx, glch1, gwp, t, cl.c0,
+                                                                cl.count, part0);
     }
 }
 
@@ -498,8 +529,10 @@ int wbp_backward_w(mld_tape *tp, const float *dsoft, float *dw, float *dllr, cud
     const size_t lsz = static_cast<size_t>(slabs) * h.n_core * W;
     const size_t dsz = static_cast<size_t>(slabs) * h.n_deg1 * W;
     const WArgs wa = wargs(d, tp->w, tp->n_types);
-    const dim3 cgrid(grid_x(static_cast<int64_t>(h.n_cn) * TPC), slabs);
     const dim3 vgrid(grid_x(static_cast<int64_t>(h.n_core) * TPC), slabs);
+    const std::vector<mld::ClassLaunch> &classes = d->g->launches[W == 8 ? 0 : (W == 16 ? 1 : (W == 32 ? 2 : 3))];
+    int32_t parts = 0;  // block partials of one adjoint check pass
+    for (const mld::ClassLaunch &cl : classes) parts += cl.blocks * slabs;
 
     // dloss/dL^T: into dL_ch (the posterior is L_ch + sum r^T) and onto r^T
     if (lsz) MLD_CUDA(cudaMemsetAsync(tp->glch, 0, lsz * sizeof(float), st));
@@ -536,12 +569,16 @@ int wbp_backward_w(mld_tape *tp, const float *dsoft, float *dw, float *dllr, cud
         for (int t = t1; t > t0; --t) {
             const float *rp = tp->seg_r + (t - 1 - t0) * rsz;
             const float *lvp = tp->seg_lv + (t - 1 - t0) * lsz;
-            if (h.n_cn > 0) {
-                kw_check_bwd<W><<<cgrid, kBlock, 0, st>>>(wa, rp, lvp, tp->gr, t == T ? tp->gd1 : nullptr, tp->gx,
-                                                          tp->glch1, tp->gwp, t);
-                MLD_LAUNCHED("kw_check_bwd");
-                kw_reduce_dw<<<1, kReduceThreads, 0, st>>>(tp->gwp, cgrid.x * cgrid.y, tp->n_types,
-                                               dw + static_cast<size_t>(t - 1) * tp->n_types);
+            if (parts > 0) {
+                int32_t part0 = 0;
+                for (const mld::ClassLaunch &cl : classes) {
+                    launch_check_bwd<W>(wa, cl, rp, lvp, tp->gr, t == T ? tp->gd1 : nullptr, tp->gx, tp->glch1,
+                                        tp->gwp, t, slabs, part0, st);
+                    MLD_LAUNCHED("kw_check_bwd");
+                    part0 += cl.blocks * slabs;
+                }
+                kw_reduce_dw<<<1, kReduceThreads, 0, st>>>(tp->gwp, parts, tp->n_types,
+                                                           dw + static_cast<size_t>(t - 1) * tp->n_types);
                 MLD_LAUNCHED("kw_reduce_dw");
             } else {
                 MLD_CUDA(cudaMemsetAsync(dw + static_cast<size_t>(t - 1) * tp->n_types, 0,
@@ -617,7 +654,9 @@ int mld_wbp_forward(mld_decoder *d, const float *llr, const uint8_t *syndrome, i
         if (s == MLD_OK) s = talloc(&tp->glch, lsz);
         if (s == MLD_OK) s = talloc(&tp->glch1, dsz);
         if (s == MLD_OK) s = talloc(&tp->gd1, dsz);
-        tp->gwp_blocks = grid_x(static_cast<int64_t>(h.n_cn) * (W / kK)) * slabs;
+        tp->gwp_blocks = 0;
+        for (const mld::ClassLaunch &cl : d->g->launches[W == 8 ? 0 : (W == 16 ? 1 : (W == 32 ? 2 : 3))])
+            tp->gwp_blocks += cl.blocks * slabs;
         if (s == MLD_OK) s = talloc(&tp->gwp, static_cast<size_t>(std::max(1, tp->gwp_blocks)) * n_types);
         if (s == MLD_OK) {
             cudaError_t e = cudaMemcpyAsync(tp->w, w, sizeof(float) * T * n_types, cudaMemcpyDeviceToDevice, st);
