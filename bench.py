@@ -178,12 +178,13 @@ class ClockSampler:
     def __init__(self, uuid: str | None):
         self.uuid = (uuid or "").lower().replace("gpu-", "")
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="mld_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
@@ -201,7 +202,10 @@ class ClockSampler:
             self.proc.kill()
         self.f.close()
         rows = []
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        os.unlink(self.path)
+        for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 10:
                 continue
@@ -348,7 +352,7 @@ def run_wbp(a, world, rank, local):
     losses = [float(x.detach()) for x in losses]
     val_after = val_loss()
 
-    # judge: FER at n = 10^6 of unit weights (plain BP) and of the trained weights
+    # held-out evaluation: FER at n = 10^6 of unit weights (plain BP) and of the trained weights
     n_ev, B_ev = 1_000_000, 64
     wl = make_workload(0.1, n_ev, B_ev, 11, 30_000, beta=beta)
     G_ev = mld.Graph.from_edges(wl.graph)
@@ -367,7 +371,7 @@ def run_wbp(a, world, rank, local):
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MET ensemble, BIAWGN samples)",
         "config": {"workload": f"rate 0.1, n={n_tr}, {B_tr} codewords, T={T}, checkpoint every {k}, "
-                               f"20x3 weights, Adam lr 0.003, beta={beta}; judged at n={n_ev}, {B_ev} codewords"},
+                               f"20x3 weights, Adam lr 0.003, beta={beta}; evaluated at n={n_ev}, {B_ev} codewords"},
         "val_loss_unit_weights": val_before, "val_loss_trained": val_after,
         "train_loss_first5": float(np.mean(losses[:5])), "train_loss_last5": float(np.mean(losses[-5:])),
         "fer_plain_T20": fer["plain"], "fer_weighted_T20": fer["weighted"],
