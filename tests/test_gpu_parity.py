@@ -145,6 +145,25 @@ def test_decode_matches_oracle(mld, msg, beta, iters, et):
         assert (_np(out["bits"]) == ref["bits"]).mean() >= 0.9999
 
 
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_early_termination_decisions_only(mld, msg):
+    # without soft output, a degree-1 decision compares o with phi(|L_ch|)
+    # instead of taking the sign of L_ch + phi(o): the two differ only where
+    # |L_ch| and |r| agree to within the phi fit's error, so a frame's
+    # trajectory may drift (as between float and half), and the criteria are
+    # those of near-threshold frames, plus agreement with the soft-output run
+    w = make_workload(0.1, 4096, 32, 1, 1300, beta=0.36)
+    g = mld.Graph.from_edges(w.graph)
+    dec = mld.Decoder(g, 32, msg_dtype=msg)
+    soft = dec.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=40, early_term=True, want_post=True)
+    hard = dec.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=40, early_term=True)
+    ref = oracle.decode_y(w.graph, w.y, w.sigma, w.s, iters=40, early_term=True)
+    _check_frames(hard, ref, w.graph, w.s, msg, near_threshold=True)
+    both = _np(soft["converged"]).astype(bool) & _np(hard["converged"]).astype(bool)
+    assert (_np(soft["converged"]) == _np(hard["converged"])).mean() >= 0.9
+    assert np.array_equal(_np(soft["bits"])[both], _np(hard["bits"])[both])
+
+
 @pytest.mark.parametrize("B,W,msg", [(5, 32, "f32"), (37, 16, "f32"), (3, 8, "f16"), (70, 64, "f16")])
 def test_ragged_batches_and_slab_widths(mld, B, W, msg):
     g0 = preset_graph(0.05, 3000, 4)
