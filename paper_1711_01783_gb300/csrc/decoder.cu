@@ -55,6 +55,12 @@ void build_class_tables(mld_graph *g) {
             out.push_back(l);
         }
     }
+    // the fused syndrome check needs every check in a register class (the
+    // checks without edges and the irregular class are not covered)
+    g->fusable = true;
+    for (const mld::CheckClass &cl : g->h.classes)
+        if (cl.dc < 0 || cl.dd > 1 || cl.dc + cl.dd > mld::kMaxRegDeg || (cl.dc == 0 && cl.dd == 0))
+            g->fusable = false;
 }
 
 namespace {
@@ -110,10 +116,18 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         if (s != MLD_OK) return s;
     }
 
+    // degree-1 decisions: two buffers, written by iterations of each parity
+    // (a codeword's output is read from the one of its last iteration)
+    const size_t h1 = static_cast<size_t>(slabs) * h.n_deg1 * (W / 8);
+    auto hb1_of = [&](int32_t l) { return d->hb1 + static_cast<size_t>(l & 1) * h1; };
     CnArgs ca{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, h.e_core,
               d->r, d->Lv, d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done,
-              d->lmax_i, d->amin_i, 0, et ? 1 : 0};
-    const bool hard1 = et && !post;  // degree-1 decisions only
+              d->lmax_i, d->amin_i, 0, et ? 1 : 0, 0, batch, d->hb1, d->fail};
+    // early termination without soft output: degree-1 decisions only, and
+    // the syndrome of iteration l-1 formed inside check pass l (every check
+    // in a register class; otherwise a separate syndrome check per iteration)
+    const bool hard1 = et && !post;
+    const bool fused = hard1 && g->fusable;
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
                d->fail, d->done, et ? 1 : 0, batch};
@@ -140,6 +154,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         MLD_CUDA(cudaMemsetAsync(d->fail, 0, sizeof(uint32_t) * slabs * DW, st));
         if (h.n_cn > 0) {
             sa.et = et_mode ? 1 : 0;
+            sa.hb1 = hb1_of(l);
             int s = timed_launch(d, kClsSyn, st, "k_syndrome_check", [&] {
                 k_syndrome_check<W><<<syn_grid, kBlock, 0, st>>>(sa);
             });
@@ -172,7 +187,12 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     for (int32_t l = 1; l <= iters; ++l) {
         const bool last = (l == iters);
         ca.final_pass = (last || et) ? 1 : 0;
+        ca.hb1 = hb1_of(l);
+        ca.hb1_prev = hb1_of(l - 1);
+        ca.fail_prev = d->fail + static_cast<size_t>((l - 1) & 1) * slabs * DW;
+        ca.fuse = (fused && l >= 2) ? 1 : 0;
         d->sample_now = ((l - 1) % d->timing_every) == 0;
+        if (ca.fuse) MLD_CUDA(cudaMemsetAsync(ca.fail_prev, 0, sizeof(uint32_t) * slabs * DW, st));
         {
             int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
                 if (big < 0) {
@@ -192,21 +212,29 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
             }, static_cast<int>(launches.size()));
             if (s != MLD_OK) return s;
         }
-        va.want_bits = (last || et) ? 1 : 0;
+        if (ca.fuse) {  // codewords whose iteration l-1 satisfied every check stop there
+            int s = timed_launch(d, kClsSyn, st, "k_lane_update", [&] {
+                k_lane_update<W><<<lane_blocks, 128, 0, st>>>(d->done, ca.fail_prev, d->iters, d->conv, batch,
+                                                               l - 1, 1);
+            });
+            if (s != MLD_OK) return s;
+        }
+        va.want_bits = (last || (et && !fused)) ? 1 : 0;
         if (h.n_core > 0) {
             int s = timed_launch(d, kClsVar, st, "k_var_update", [&] {
                 k_var_update<MsgT, W><<<vn_grid, kBlock, 0, st>>>(va);
             });
             if (s != MLD_OK) return s;
         }
-        if (et || last) {
+        if ((et && !fused) || last) {
             int s = syndrome_round(l, et);
             if (s != MLD_OK) return s;
         }
     }
 
     d->sample_now = true;
-    OutArgs oa{g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, d->hb1, bits, post, d->scale_out};
+    OutArgs oa{g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, d->hb1, d->iters, h1, bits, post,
+               d->scale_out};
     if (h.n_vn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_deinterleave_out", [&] {
             k_deinterleave_out<W><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(oa);
@@ -426,7 +454,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     if (s == MLD_OK) s = dalloc(&d->post1, S * h.n_deg1 * W);
     if (s == MLD_OK) s = dalloc(&d->phi1, S * h.n_deg1 * W);
     if (s == MLD_OK) s = dalloc(&d->hb_core, S * h.n_core * NB);
-    if (s == MLD_OK) s = dalloc(&d->hb1, S * h.n_deg1 * NB);
+    if (s == MLD_OK) s = dalloc(&d->hb1, 2 * S * h.n_deg1 * NB);  // two buffers (iteration parity)
     if (s == MLD_OK) s = dalloc(&d->sbits, S * h.n_cn * NB);
     if (s == MLD_OK) s = dalloc(&d->done, S * DW);
     if (s == MLD_OK) s = dalloc(&d->fail, 2 * S * DW);  // two buffers (iteration parity) for plans
@@ -598,7 +626,7 @@ NoallocLayout noalloc_layout(const mld::HostGraph &h, int W, size_t msz, int sla
     L.post1 = take(S * h.n_deg1 * W * sizeof(float));
     L.phi1 = take(S * h.n_deg1 * W * sizeof(float));
     L.hb_core = take(S * h.n_core * NB);
-    L.hb1 = take(S * h.n_deg1 * NB);
+    L.hb1 = take(2 * S * h.n_deg1 * NB);
     L.sbits = take(S * h.n_cn * NB);
     L.done = take(S * DW * sizeof(uint32_t));
     L.fail = take(2 * S * DW * sizeof(uint32_t));

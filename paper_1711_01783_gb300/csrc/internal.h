@@ -76,4 +76,6 @@ struct mld_graph {
     uint8_t *etype_core = nullptr, *etype_deg1 = nullptr;
     // check-update launches per slab width (8, 16, 32, 64)
     std::vector<mld::ClassLaunch> launches[4];
+    // every check is in a register class (enables the fused syndrome check)
+    bool fusable = false;
 };

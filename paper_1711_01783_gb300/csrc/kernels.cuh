@@ -222,11 +222,19 @@ struct CnArgs {
     const float *lch1;     // [slab][n_deg1][W] degree-1 channel LLRs
     const float *phi1;     // [slab][n_deg1][W] phi(|L_ch|) with the sign of L_ch (constant)
     float *post1;          // [slab][n_deg1][W] degree-1 posteriors (final / ET pass)
-    uint8_t *hb1;          // [slab][n_deg1][W/8] degree-1 hard decisions
+    uint8_t *hb1;          // [slab][n_deg1][W/8] degree-1 hard decisions written by this pass
     const uint8_t *sbits;  // [slab][n_cn][W/8] syndrome bits
     const uint32_t *done;  // [slab][ceil(W/32)] converged lanes (ET)
     float lmax, amin;
     int final_pass, et;
+    // Fused syndrome check (early termination without soft output): this
+    // pass also forms the syndrome of the previous iteration from the signs
+    // of the posteriors it reads and the previous degree-1 decisions, and ORs
+    // the failing codewords into fail_prev.
+    int fuse;
+    int32_t batch;              // codewords (later lanes are padding)
+    const uint8_t *hb1_prev;    // degree-1 decisions of the previous iteration
+    uint32_t *fail_prev;        // [slab][ceil(W/32)] fail words of the previous iteration
 };
 
 template <typename MsgT, int W>
@@ -290,10 +298,12 @@ constexpr uint32_t kSign = 0x80000000u;
 // terms in registers), codewords lane0 .. lane0+3 of the slab.  A thread past
 // the class end works on its last check and stores nothing (so a whole
 // shuffle pair stays active).  HARD1: a degree-1 VN gets its decision only,
-// not its posterior (early termination without soft output).
+// not its posterior (early termination without soft output); with a.fuse the
+// call also returns the previous iteration's syndrome failures of the check
+// for the thread's 4 codewords (bit k: codeword lane0 + k), else 0.
 template <typename MsgT, int W, int DC, int DD, bool HARD1 = false>
-__device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
-                                              int slab) {
+__device__ __forceinline__ uint32_t check_regular(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
+                                                  int slab) {
     constexpr int NB = W / 8;
     constexpr int D = DC + DD;
     constexpr int dc = DC;
@@ -323,12 +333,17 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
     // degree-1 VN q is its channel LLR, whose f was formed once on entry.
     float f[D][kK];
     uint32_t par[kK];
+    uint32_t lvs[kK] = {0u, 0u, 0u, 0u};  // sign parity of the posteriors read (fused syndrome)
 #pragma unroll
     for (int kk = 0; kk < kK; ++kk) par[kk] = ((sb >> kk) & 1u) << 31;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         if (i < dc) {
             const float4 lv = ldf4(lvb + static_cast<size_t>(vidx[i]) * W);
+            if constexpr (HARD1) {
+#pragma unroll
+                for (int kk = 0; kk < kK; ++kk) lvs[kk] ^= fbits(f4get(lv, kk));
+            }
             const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
             const float4 q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
             // phi(|q|) floored at amin = phi(lmax) is phi of |q| clamped above at
@@ -422,6 +437,42 @@ __device__ __forceinline__ void check_regular(const CnArgs &a, const ClassLaunch
             for (int kk = 0; kk < kK; ++kk) suf[kk] = (i == D - 1) ? fabsf(f[i][kk]) : suf[kk] + fabsf(f[i][kk]);
         }
     }
+    uint32_t fail = 0;
+    if constexpr (HARD1) {
+        if (a.fuse && valid) {
+            // previous iteration: s_c XOR the decisions of the check's VNs
+            // (core: posterior < 0, the sign read above; degree-1: stored bit)
+            uint32_t x = sb & 0xFu;
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) x ^= (lvs[kk] >> 31) << kk;
+            if (DD == 1)
+                x ^= (static_cast<uint32_t>(a.hb1_prev[(static_cast<size_t>(slab) * a.n_deg1 + s0) * NB + lane0 / 8]) >>
+                      (lane0 & 7)) & 0xFu;
+            const int lanes = a.batch - slab * W - lane0;  // real codewords among the 4
+            const uint32_t real = lanes >= kK ? 0xFu : (lanes > 0 ? (1u << lanes) - 1u : 0u);
+            fail = x & real & ~donenib;
+        }
+    }
+    return fail;
+}
+
+// ORs the fused syndrome failures of a block's threads (4 codewords each,
+// at lane0) into the fail words of the slab: warp reduction, then one atomic
+// per word and warp.  Every thread of the block must call it.
+template <int W>
+__device__ __forceinline__ void flush_fail(uint32_t *fail_slab, uint32_t nib, int lane0) {
+    constexpr int DW = (W + 31) / 32;
+    uint32_t lo = lane0 < 32 ? nib << lane0 : 0u;
+    uint32_t hi = lane0 >= 32 ? nib << (lane0 - 32) : 0u;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        lo |= __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        if (DW > 1) hi |= __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (lo) atomicOr(fail_slab, lo);
+        if (DW > 1 && hi) atomicOr(fail_slab + 1, hi);
+    }
 }
 
 // Checks of any degree, edges read through cptr/dptr; leave-one-out sums as
@@ -493,25 +544,38 @@ __device__ __forceinline__ void check_irregular(const CnArgs &a, const ClassLaun
 // The 7- and 8-term classes (80 registers) take one check per thread.
 template <int D> constexpr bool kLoopedClass = D <= 6;
 
+// The threads of a class launch (t0: thread index in the slab's grid of
+// `blocks` blocks): looped classes step through their checks, the others take
+// one; with HARD1 the fused syndrome failures are ORed into a.fail_prev.
+template <typename MsgT, int W, int DC, int DD, bool HARD1>
+__device__ __forceinline__ void check_class_body(const CnArgs &a, const ClassLaunch &cl, int64_t t0,
+                                                 int32_t blocks, int slab) {
+    constexpr int TPC = W / kK;
+    const int lane0 = static_cast<int>(t0 % TPC) * kK;
+    uint32_t fail = 0;
+    if constexpr (kLoopedClass<DC + DD>) {
+        // a capped grid; each thread takes every stride-th check with the
+        // same lanes, so its set-up is shared by several checks.  Both
+        // threads of a shuffle pair belong to one check and leave together.
+        const int32_t jstride = blocks * (kBlock / TPC);
+        for (int32_t j = static_cast<int32_t>(t0 / TPC); j < cl.count; j += jstride)
+            fail |= check_regular<MsgT, W, DC, DD, HARD1>(a, cl, j, lane0, slab);
+    } else {
+        fail = check_regular<MsgT, W, DC, DD, HARD1>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
+    }
+    if constexpr (HARD1) {
+        if (a.fuse) flush_fail<W>(a.fail_prev + slab * ((W + 31) / 32), fail, lane0);
+    }
+}
+
 // One check class per launch, its shape (DC, DD) a compile-time constant: the
 // register arrays are sized exactly and only this class's code is hot.
 template <typename MsgT, int W, int DC, int DD, bool HARD1>
 __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
-    constexpr int TPC = W / kK;
-    const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int lane0 = static_cast<int>(t0 % TPC) * kK;
-    if constexpr (kLoopedClass<DC + DD>) {
-        // a capped grid; each thread takes every stride-th check with the
-        // same lanes, so its set-up is shared by several checks.  Both
-        // threads of a shuffle pair belong to one check and leave together.
-        const int32_t jstride = static_cast<int32_t>(gridDim.x) * (kBlock / TPC);
-        for (int32_t j = static_cast<int32_t>(t0 / TPC); j < cl.count; j += jstride)
-            check_regular<MsgT, W, DC, DD, HARD1>(a, cl, j, lane0, slab);
-    } else {
-        check_regular<MsgT, W, DC, DD, HARD1>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
-    }
+    check_class_body<MsgT, W, DC, DD, HARD1>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
+                                             static_cast<int32_t>(gridDim.x), slab);
 }
 
 template <typename MsgT, int W>
@@ -525,7 +589,8 @@ __global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, Cla
 // run the register kernel for their shape; any other class (possible in
 // caller graphs, not in the MET ensembles) runs the streaming kernel.
 // cap_blocks: grid width for the looped classes (a few waves of the GPU);
-// hard1: degree-1 decisions only (see check_regular).
+// hard1: early termination without soft output (degree-1 decisions only, and
+// the fused syndrome check when ca.fuse; see check_regular).
 template <typename MsgT, int W>
 void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks,
                         bool hard1) {
@@ -536,7 +601,7 @@ void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cuda
 #define MLD_CASE(DCV, DDV)                                                                          \
     case (DCV) * 2 + (DDV):                                                                         \
         static_assert(kLoopedClass<(DCV) + (DDV)> == ((DCV) + (DDV) <= 6), "grid choice");         \
-        if (hard1) k_check_update<MsgT, W, DCV, DDV, (DDV) == 1><<<g, kBlock, 0, st>>>(ca, cl);   \
+        if (hard1) k_check_update<MsgT, W, DCV, DDV, true><<<g, kBlock, 0, st>>>(ca, cl);          \
         else k_check_update<MsgT, W, DCV, DDV, false><<<g, kBlock, 0, st>>>(ca, cl);              \
         return;
     if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
@@ -593,6 +658,18 @@ __device__ __forceinline__ void var_body(const VnArgs &a, int64_t t, int slab) {
     for (; j < j1; ++j) {
         const float4 ra = Msg<MsgT>::load(rb + static_cast<size_t>(__ldg(a.vedge + j)) * W);
         acc.x += ra.x; acc.y += ra.y; acc.z += ra.z; acc.w += ra.w;
+    }
+    if (a.et) {
+        // converged lanes keep the posterior of their last iteration (with a
+        // fused syndrome check a lane is marked after its messages moved on)
+        const uint32_t dn = done_nibble<W>(a.done, slab, lane0);
+        if (dn) {
+            const float4 old = *reinterpret_cast<const float4 *>(a.Lv + vrow);
+            if (dn & 1) acc.x = old.x;
+            if (dn & 2) acc.y = old.y;
+            if (dn & 4) acc.z = old.z;
+            if (dn & 8) acc.w = old.w;
+        }
     }
     *reinterpret_cast<float4 *>(a.Lv + vrow) = acc;
     if (a.want_bits) {
@@ -844,6 +921,8 @@ struct OutArgs {
     int32_t n_vn, n_core, n_deg1, batch;
     const float *Lv, *post1;
     const uint8_t *hb1;  // degree-1 decisions (post1 is formed only for soft output)
+    const int32_t *iters;  // iterations used per codeword: hb1 buffer (iters & 1), or null (buffer 0)
+    size_t hb1_stride;     // bytes between the two hb1 buffers
     uint8_t *bits;   // [B][n_vn]
     float *post;     // [B][n_vn] or null
     float scale;     // internal units -> nats
@@ -868,7 +947,9 @@ __device__ __forceinline__ void deinterleave_body(const OutArgs &a, int tile_x, 
             } else {
                 const size_t s = static_cast<size_t>(slab) * a.n_deg1 + (u - a.n_core);
                 if (a.post) v = a.post1[s * W + w];
-                bit = (a.hb1[s * NB + w / 8] >> (w & 7)) & 1u;
+                const int b = slab * W + w;
+                const size_t buf = (a.iters && b < a.batch) ? static_cast<size_t>(a.iters[b] & 1) * a.hb1_stride : 0;
+                bit = (a.hb1[buf + s * NB + w / 8] >> (w & 7)) & 1u;
             }
         }
         tile[jj][w] = v;

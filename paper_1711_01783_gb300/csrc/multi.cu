@@ -45,33 +45,40 @@ __device__ __forceinline__ int find_seg(const Seg *segs, int nseg) {
     return k;
 }
 
+// Check arguments of job j at iteration l: the degree-1 decision buffer of
+// l's parity, and for the fused syndrome check (seg flag 2, l >= 2) the
+// buffers of iteration l-1.
+template <int W>
+__device__ __forceinline__ CnArgs job_cn(const JobDev &j, const Seg &sg, int32_t l) {
+    constexpr int DW = (W + 31) / 32;
+    CnArgs a = j.cn;
+    a.final_pass = sg.flags & 1;
+    const size_t h1 = static_cast<size_t>(j.slabs) * a.n_deg1 * (W / 8);
+    a.hb1 = j.cn.hb1 + static_cast<size_t>(l & 1) * h1;
+    a.hb1_prev = j.cn.hb1 + static_cast<size_t>((l - 1) & 1) * h1;
+    a.fail_prev = j.fail + static_cast<size_t>((l - 1) & 1) * j.slabs * DW;
+    a.fuse = ((sg.flags & 2) && l >= 2) ? 1 : 0;
+    return a;
+}
+
 template <typename MsgT, int W, int DC, int DD, bool HARD1>
 __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6))
-    km_check(const JobDev *jobs, const Seg *segs, int nseg) {
+    km_check(const JobDev *jobs, const Seg *segs, int nseg, int32_t l) {
     const Seg sg = segs[find_seg(segs, nseg)];
-    CnArgs a = jobs[sg.job].cn;
-    a.final_pass = sg.flags & 1;
+    const CnArgs a = job_cn<W>(jobs[sg.job], sg, l);
     const int local = blockIdx.x - sg.block0;
     const int slab = local / sg.bps;
     if (a.et && slab_all_done<W>(a.done, slab)) return;
-    constexpr int TPC = W / kK;
-    const int64_t t0 = static_cast<int64_t>(local % sg.bps) * blockDim.x + threadIdx.x;
-    const int lane0 = static_cast<int>(t0 % TPC) * kK;
-    if constexpr (kLoopedClass<DC + DD>) {
-        // the segment's grid is capped (build_plan); threads loop over checks
-        const int32_t jstride = sg.bps * (kBlock / TPC);
-        for (int32_t j = static_cast<int32_t>(t0 / TPC); j < sg.cl.count; j += jstride)
-            check_regular<MsgT, W, DC, DD, HARD1>(a, sg.cl, j, lane0, slab);
-    } else {
-        check_regular<MsgT, W, DC, DD, HARD1>(a, sg.cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
-    }
+    // the segment's grid is capped for looped classes (build_plan)
+    check_class_body<MsgT, W, DC, DD, HARD1>(a, sg.cl, static_cast<int64_t>(local % sg.bps) * blockDim.x + threadIdx.x,
+                                             sg.bps, slab);
 }
 
 template <typename MsgT, int W>
-__global__ void __launch_bounds__(kBlock) km_check_irregular(const JobDev *jobs, const Seg *segs, int nseg) {
+__global__ void __launch_bounds__(kBlock) km_check_irregular(const JobDev *jobs, const Seg *segs, int nseg,
+                                                             int32_t l) {
     const Seg sg = segs[find_seg(segs, nseg)];
-    CnArgs a = jobs[sg.job].cn;
-    a.final_pass = sg.flags & 1;
+    const CnArgs a = job_cn<W>(jobs[sg.job], sg, l);
     const int local = blockIdx.x - sg.block0;
     const int slab = local / sg.bps;
     if (a.et && slab_all_done<W>(a.done, slab)) return;
@@ -97,6 +104,7 @@ __global__ void __launch_bounds__(kBlock) km_syndrome(const JobDev *jobs, const 
     const JobDev &j = jobs[sg.job];
     SynArgs a = j.sy;
     a.fail = j.fail + parity * j.slabs * DW;
+    a.hb1 = j.sy.hb1 + static_cast<size_t>(parity) * j.slabs * a.n_deg1 * (W / 8);
     const int local = blockIdx.x - sg.block0;
     const int slab = local / sg.bps;
     if (a.et && slab_all_done<W>(a.done, slab)) return;
@@ -178,8 +186,8 @@ void launch_check_op(const mld_plan *p, const Op &op, cudaStream_t st) {
     const Seg *S = p->d_segs + op.seg0;
 #define MLD_CASE(DCV, DDV)                                                                          \
     if (op.dc == (DCV) && op.dd == (DDV)) {                                                         \
-        if (op.hard1) km_check<MsgT, W, DCV, DDV, (DDV) == 1><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg); \
-        else km_check<MsgT, W, DCV, DDV, false><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg);      \
+        if (op.hard1) km_check<MsgT, W, DCV, DDV, true><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg, op.l); \
+        else km_check<MsgT, W, DCV, DDV, false><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg, op.l);      \
         return;                                                                                     \
     }
     MLD_CASE(1, 0) MLD_CASE(2, 0) MLD_CASE(3, 0) MLD_CASE(4, 0)
@@ -187,7 +195,7 @@ void launch_check_op(const mld_plan *p, const Op &op, cudaStream_t st) {
     MLD_CASE(0, 1) MLD_CASE(1, 1) MLD_CASE(2, 1) MLD_CASE(3, 1)
     MLD_CASE(4, 1) MLD_CASE(5, 1) MLD_CASE(6, 1) MLD_CASE(7, 1)
 #undef MLD_CASE
-    km_check_irregular<MsgT, W><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg);
+    km_check_irregular<MsgT, W><<<op.blocks, kBlock, 0, st>>>(J, S, op.nseg, op.l);
 }
 
 template <int W>
@@ -261,14 +269,16 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
         JobDev x{};
         const bool y_mode = jb.sigma != nullptr;
         x.cn = CnArgs{d->g->cptr, d->g->col, d->g->dptr, h.n_cn, h.n_core, h.n_deg1, h.e_core, d->r, d->Lv,
-                      d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done, d->lmax_i, d->amin_i, 0, et ? 1 : 0};
+                      d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done, d->lmax_i, d->amin_i, 0, et ? 1 : 0,
+                      0, jb.batch, d->hb1, d->fail};
         x.vn = VnArgs{d->g->vptr, d->g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0,
                       et ? 1 : 0};
         x.sy = SynArgs{d->g->cptr, d->g->col, d->g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core,
                        d->hb1, d->fail, d->done, et ? 1 : 0, jb.batch};
         x.in = InArgs{jb.in, y_mode ? jb.sigma : nullptr, d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch,
                       d->lmax, d->scale_in, d->lmax_i, d->amin_i, d->lch, d->Lv, d->lch1, d->post1, d->phi1};
-        x.out = OutArgs{d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch, d->Lv, d->post1, d->hb1, jb.bits_out,
+        x.out = OutArgs{d->g->unit, h.n_vn, h.n_core, h.n_deg1, jb.batch, d->Lv, d->post1, d->hb1, jb.iters_used,
+                        static_cast<size_t>(slabs) * h.n_deg1 * (W / 8), jb.bits_out,
                         jb.post_out, d->scale_out};
         x.syn = jb.syndrome;
         x.cint = d->g->cint;
@@ -395,14 +405,20 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
         if (!zero.empty()) syndrome_round(zero, 0);
     }
 
+    // early termination without soft output: degree-1 decisions only, and for
+    // graphs whose checks are all in register classes the syndrome of
+    // iteration l-1 is formed inside check pass l (then only the last
+    // iteration gets a separate syndrome check)
+    auto hard1_job = [&](int32_t j) { return et && !jobs[j].post_out; };
+    auto fused_job = [&](int32_t j) { return hard1_job(j) && jobs[j].decoder->g->fusable; };
     for (int32_t l = 1; l <= lmax_iters; ++l) {
-        std::vector<int32_t> active, checked;
+        std::vector<int32_t> active, checked, lanes;
         for (int32_t j = 0; j < n_jobs; ++j)
             if (jobs[j].max_iters >= l) active.push_back(j);
         for (int32_t j : active) {
             const mld_decoder *d = jobs[j].decoder;
             const int half = d->msg == MLD_MSG_F16;
-            const int fl = (et || l == jobs[j].max_iters) ? 1 : 0;
+            const int fl = ((et || l == jobs[j].max_iters) ? 1 : 0) | (fused_job(j) ? 2 : 0);
             for (const ClassLaunch &cl : d->g->launches[width_index(d->W)]) {
                 const int dd = cl.deg - cl.dc;
                 const bool regular = cl.dc >= 0 && (dd == 0 || dd == 1);
@@ -410,11 +426,22 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
                 const bool looped = regular && cl.deg <= 6;
                 Seg s = seg(j, looped ? std::max(1, std::min(cl.blocks, sm_count * 16)) : cl.blocks, jd[j].slabs, fl);
                 s.cl = cl;
-                const int hard1 = (et && !jobs[j].post_out && regular && dd == 1) ? 1 : 0;
+                const int hard1 = (hard1_job(j) && regular) ? 1 : 0;
                 groups[Key{kOpCheck, half, d->W, regular ? cl.dc : -1, regular ? dd : -1, hard1}].push_back(s);
             }
+            if (fused_job(j) && l >= 2) lanes.push_back(j);
         }
         flush(groups, l, 0);
+        // the codewords of fused jobs whose iteration l-1 satisfied every check
+        // stop there (the lane op also clears the other fail buffer)
+        if (!lanes.empty()) {
+            for (int32_t j : lanes) {
+                const mld_decoder *d = jobs[j].decoder;
+                const int nl = std::max(jd[j].batch, jd[j].slabs * ((d->W + 31) / 32));
+                groups[Key{kOpLane, 0, d->W, 0, 0, 0}].push_back(seg(j, (nl + kBlock - 1) / kBlock, 1, 0));
+            }
+            flush(groups, l - 1, (l - 1) & 1);
+        }
         for (int32_t j : active) {
             const mld_decoder *d = jobs[j].decoder;
             const int half = d->msg == MLD_MSG_F16;
@@ -422,7 +449,7 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
             const int tpc = d->W / kK;
             const int bps = grid_x(static_cast<int64_t>(d->g->h.n_core) * tpc);
             if (d->g->h.n_core > 0) groups[Key{kOpVar, half, d->W, 0, 0, 0}].push_back(seg(j, bps, jd[j].slabs, fl));
-            if (fl) checked.push_back(j);
+            if (fl && (!fused_job(j) || l == jobs[j].max_iters)) checked.push_back(j);
         }
         flush(groups, l, 0);
         if (!checked.empty()) syndrome_round(checked, l);

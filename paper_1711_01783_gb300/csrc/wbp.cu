@@ -511,7 +511,8 @@ int wbp_forward_w(mld_decoder *d, const float *llr, const uint8_t *syn, int32_t 
     const WArgs wa = wargs(d, w, n_types);
     int s = forward_iters<W>(d, wa, static_cast<float *>(d->r), d->Lv, 0, T, T, slabs, st, tape, nullptr, nullptr);
     if (s != MLD_OK) return s;
-    OutArgs oa{d->g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, d->hb1, d->bits_stage, soft, 1.f};
+    OutArgs oa{d->g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, d->hb1, nullptr, 0, d->bits_stage,
+               soft, 1.f};
     if (h.n_vn > 0) {
         k_deinterleave_out<W><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(oa);
         MLD_LAUNCHED("k_deinterleave_out");
