@@ -138,11 +138,6 @@ __device__ __forceinline__ float4 phi4_floor(float4 x, float lo) {
                        max3f(phi_small<F>(x.w), phi_large<F>(x.w), lo));
 }
 
-template <int F>
-__device__ __forceinline__ float4 phi4(float4 x) {
-    return make_float4(phi_f<F>(x.x), phi_f<F>(x.y), phi_f<F>(x.z), phi_f<F>(x.w));
-}
-
 template <typename T> struct IsHalf { static constexpr bool value = false; };
 template <> struct IsHalf<__half> { static constexpr bool value = true; };
 // the fit the decoding kernels use for a message storage type
