@@ -288,13 +288,16 @@ def test_irregular_graph_edge_cases(mld):
     assert g.stats["max_check_deg"] > 8 and g.stats["n_deg1"] == 90
     for msg in ("f32", "f16"):
         dec = mld.Decoder(g, B, msg_dtype=msg, slab_width=16)
-        for it, et in ((1, False), (12, True)):
-            out = dec.decode(_dev(L), _dev(s), iters=it, early_term=et, want_post=True)
+        for it, et, post in ((1, False, True), (12, True, True), (12, True, False)):
+            # early termination without soft output on a graph with irregular
+            # and empty checks: degree-1 decisions only, separate syndrome checks
+            out = dec.decode(_dev(L), _dev(s), iters=it, early_term=et, want_post=post)
             ref = oracle.decode(gg, L, s, iters=it, early_term=et)
             if msg == "f32" and it == 1:
                 np.testing.assert_allclose(_np(out["post"]), ref["post"], rtol=1e-4, atol=1e-3)
             assert (_np(out["bits"]) == ref["bits"]).mean() >= 0.999
             assert np.array_equal(_np(out["converged"]), ref["converged"])
+            assert np.array_equal(_syndrome_holds(gg, _np(out["bits"]), s), _np(out["converged"]).astype(bool))
 
 
 def test_invalid_arguments_raise(mld):
