@@ -241,7 +241,10 @@ __device__ __forceinline__ void emit_deg1(const CnArgs &a, int slab, int slot, i
     float4 post = make_float4(l.x + rv.x, l.y + rv.y, l.z + rv.z, l.w + rv.w);
     uint32_t nib = (post.x < 0.f) | ((post.y < 0.f) << 1) | ((post.z < 0.f) << 2) | ((post.w < 0.f) << 3);
     uint8_t *hb = a.hb1 + (static_cast<size_t>(slab) * a.n_deg1 + slot) * NB + lane0 / 8;
-    if (donenib && valid) {  // converged lanes keep the decision of their last iteration
+    // converged lanes keep their posterior and what this decision buffer
+    // holds for them (their output is read from the buffer of their last
+    // iteration's parity, which later passes leave unchanged)
+    if (donenib && valid) {
         const float4 old = *reinterpret_cast<const float4 *>(a.post1 + base);
         if (donenib & 1) post.x = old.x;
         if (donenib & 2) post.y = old.y;
@@ -256,8 +259,8 @@ __device__ __forceinline__ void emit_deg1(const CnArgs &a, int slab, int slot, i
 }
 
 // Decisions of a degree-1 VN for 4 codewords (bit k: codeword lane0 + k) into
-// its bit-sliced byte; converged lanes keep the decision of their last
-// iteration.  Both threads of a shuffle pair must call it.
+// its bit-sliced byte of this pass's buffer; converged lanes keep what the
+// byte holds (see emit_deg1).  Both threads of a shuffle pair must call it.
 template <int W>
 __device__ __forceinline__ void emit_deg1_bits(const CnArgs &a, int slab, int slot, int lane0, uint32_t nib,
                                                uint32_t donenib, bool valid) {
