@@ -339,7 +339,16 @@ int mld_decoder_timing_read(mld_decoder *d, mld_timing *out);
  * needs about 4.5 MiB per slab of 64 codewords with half messages.)
  * Set-up: the first call on each device, made with that device current,
  * looks up the array's device address (cudaGetSymbolAddress) and caches it;
- * make that first call before any stream capture on the device.
+ * make that first call before any stream capture on the device.  Under lazy
+ * module loading (CUDA_MODULE_LOADING=LAZY, the default of current CUDA) the
+ * array is only reserved when the library's module is loaded on the device,
+ * which may be that first call: make one warm-up call per device (any valid
+ * call, e.g. batch 1 with max_iters 0) before handing the device's remaining
+ * memory to another allocator, so that the 32 MiB are taken while they are
+ * still free.  If they cannot be, the call fails with MLD_ECUDA and a text
+ * naming the scratch array.  The cached address belongs to the device's
+ * primary context: after cudaDeviceReset (or any teardown of that context)
+ * it is stale, and this entry point must not be called again in the process.
  * Sharing: every call on a device uses the same array, which keeps the last
  * call's contents; each call clears what must start at zero.  Calls whose
  * work overlaps on the GPU (different streams, or host threads racing)
@@ -357,8 +366,9 @@ int mld_decode_noalloc(const mld_graph *g, int32_t msg_dtype, const float *llr,
  * update uses (the LLR-domain message map that the closing paragraph of the
  * Methods proposes to tabulate), for n inputs clamped to [phi(lmax), lmax]
  * with lmax = 25.  msg_dtype selects the variant a decoder of that message
- * storage type uses: MLD_MSG_F32 (relative error ~1e-7) or MLD_MSG_F16
- * (a shorter fit, relative error ~4e-6, below half's 2^-11 rounding).
+ * storage type uses: MLD_MSG_F32 (relative error below 2e-6, about 1.5e-7
+ * from the fit) or MLD_MSG_F16 (a shorter fit, relative error 2.0e-4, below
+ * half's 2^-11 = 4.9e-4 rounding of every stored message).
  * x and out are device float pointers [n].  Errors: MLD_EINVAL, MLD_ECUDA. */
 int mld_phi_eval(int32_t msg_dtype, const float *x, float *out, int64_t n, void *stream);
 

@@ -470,21 +470,37 @@ def decode_noalloc(graph: Graph, llr, syndrome, iters: int, msg_dtype: str = "f3
                    early_term: bool = False, want_post: bool = False, stream=None):
     """Decode without a decoder object and without allocating device memory
     in the library (mld_decode_noalloc).  Inputs are CUDA tensors; the output
-    tensors are allocated here by torch, the library allocates nothing."""
+    tensors are allocated here by torch, the library allocates nothing.
+
+    The entry point takes device pointers only, so the inputs are checked
+    here before any pointer reaches the library: both must be CUDA tensors
+    on one device, ``llr`` float32 [B, n_vn] and ``syndrome`` [B, n_cn]."""
     torch = _torch()
+    if not (_is_cuda_tensor(llr) and _is_cuda_tensor(syndrome)):
+        raise TypeError("decode_noalloc takes CUDA tensors (device pointers only)")
+    if llr.device != syndrome.device:
+        raise ValueError("llr and syndrome are on different devices")
+    if llr.dtype != torch.float32:
+        raise TypeError("llr must be float32")
+    if msg_dtype not in ("f32", "f16"):
+        raise ValueError("msg_dtype must be 'f32' or 'f16'")
+    if llr.dim() != 2 or tuple(llr.shape) != (llr.shape[0], graph.n_vn) \
+            or tuple(syndrome.shape) != (llr.shape[0], graph.n_cn):
+        raise ValueError("llr must be [B, n_vn] and syndrome [B, n_cn]")
     llr = llr.contiguous()
     syndrome = syndrome.contiguous().to(torch.uint8)
     B, n = int(llr.shape[0]), graph.n_vn
     dev = llr.device
-    out = dict(bits=torch.empty((B, n), dtype=torch.uint8, device=dev),
-               post=torch.empty((B, n), dtype=torch.float32, device=dev) if want_post else None,
-               converged=torch.empty(B, dtype=torch.uint8, device=dev),
-               iters_used=torch.empty(B, dtype=torch.int32, device=dev))
-    flags = (MLD_EARLY_TERM if early_term else 0) | MLD_DEVICE_PTRS
-    dt = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
-    _check(lib().mld_decode_noalloc(graph.handle, dt, _ptr(llr), _ptr(syndrome), B, int(iters), flags,
-                                    _ptr(out["bits"]), _ptr(out["post"]), _ptr(out["converged"]),
-                                    _ptr(out["iters_used"]), _stream_handle(stream)))
+    with torch.cuda.device(dev):
+        out = dict(bits=torch.empty((B, n), dtype=torch.uint8, device=dev),
+                   post=torch.empty((B, n), dtype=torch.float32, device=dev) if want_post else None,
+                   converged=torch.empty(B, dtype=torch.uint8, device=dev),
+                   iters_used=torch.empty(B, dtype=torch.int32, device=dev))
+        flags = (MLD_EARLY_TERM if early_term else 0) | MLD_DEVICE_PTRS
+        dt = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
+        _check(lib().mld_decode_noalloc(graph.handle, dt, _ptr(llr), _ptr(syndrome), B, int(iters), flags,
+                                        _ptr(out["bits"]), _ptr(out["post"]), _ptr(out["converged"]),
+                                        _ptr(out["iters_used"]), _stream_handle(stream)))
     return out
 
 

@@ -597,7 +597,10 @@ int noalloc_base(int dev, void **out) {
     if (!g_noalloc_base[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        if (e != cudaSuccess)
+            return cuda_fail(e, "decode_noalloc: the static scratch array could not be reserved on this device "
+                                "(its module loads with the first call under lazy loading; make a warm-up "
+                                "call before the device's memory is taken): cudaGetSymbolAddress");
         g_noalloc_base[dev] = p;
     }
     *out = g_noalloc_base[dev];

@@ -67,3 +67,39 @@ def test_null_handles_are_rejected(mld):
     assert lib.mld_graph_destroy(None) == 0 and lib.mld_decoder_destroy(None) == 0
     o = mld.Opts()
     assert lib.mld_decoder_create(None, ctypes.byref(o), ctypes.byref(ctypes.c_void_p())) == mld.MLD_EINVAL
+
+
+class _FakeCuda:
+    """Stands in for a CUDA tensor in host-only checks (nothing is launched)."""
+
+    def __init__(self, shape, dtype, device="cuda:0", is_cuda=True):
+        self.shape, self.dtype, self.device, self.is_cuda = tuple(shape), dtype, device, is_cuda
+
+    def dim(self):
+        return len(self.shape)
+
+
+def test_noalloc_binding_rejects_bad_arguments_before_the_library(mld):
+    """decode_noalloc passes device pointers only: host tensors, a wrong
+    dtype or a wrong shape must raise in the binding, before any call."""
+    import torch
+    from types import SimpleNamespace
+    g = SimpleNamespace(n_vn=10, n_cn=4, handle=None)
+    good_l = _FakeCuda((3, 10), torch.float32)
+    good_s = _FakeCuda((3, 4), torch.uint8)
+    with pytest.raises(TypeError):
+        mld.decode_noalloc(g, torch.zeros((3, 10)), torch.zeros((3, 4), dtype=torch.uint8), 5)
+    with pytest.raises(TypeError):
+        mld.decode_noalloc(g, np.zeros((3, 10), np.float32), good_s, 5)
+    with pytest.raises(TypeError):
+        mld.decode_noalloc(g, _FakeCuda((3, 10), torch.float64), good_s, 5)
+    with pytest.raises(ValueError):
+        mld.decode_noalloc(g, _FakeCuda((3, 9), torch.float32), good_s, 5)
+    with pytest.raises(ValueError):
+        mld.decode_noalloc(g, good_l, _FakeCuda((3, 5), torch.uint8), 5)
+    with pytest.raises(ValueError):
+        mld.decode_noalloc(g, good_l, _FakeCuda((2, 4), torch.uint8), 5)
+    with pytest.raises(ValueError):
+        mld.decode_noalloc(g, good_l, _FakeCuda((3, 4), torch.uint8, device="cuda:1"), 5)
+    with pytest.raises(ValueError):
+        mld.decode_noalloc(g, good_l, good_s, 5, msg_dtype="bf16")

@@ -3,8 +3,9 @@
 Tolerances (derived from the arithmetic):
 * phi: float evaluation of the two polynomial pieces on top of MUFU lg2/ex2
   (relative error about 2^-22 each) -- relative error below 2e-6 on
-  [phi(25), 25] for the fit used with float messages, below 1e-5 for the
-  shorter fit used with half messages (fit error 3.7e-6).
+  [phi(25), 25] for the fit used with float messages, below 2.5e-4 for the
+  shorter fit used with half messages (fit error 2.0e-4, under half's 2^-11
+  rounding of each stored message).
 * One iteration, float messages: each check output carries a few float
   roundings through phi and the prefix/suffix sums; a posterior sums up to
   d_v of them.  Bound used: |dL| <= 1e-4 + 1e-5 |L|.

@@ -29,13 +29,17 @@ def _llr32(w):
     return (2.0 * w.y.astype(np.float64) / (w.sigma.astype(np.float64)[:, None] ** 2)).astype(np.float32)
 
 
-def _noalloc(mld, g, msg, llr, s, iters, early_term):
+def _outputs(B, n):
+    return (torch.empty((B, n), dtype=torch.uint8, device="cuda"),
+            torch.empty((B, n), dtype=torch.float32, device="cuda"),
+            torch.empty(B, dtype=torch.uint8, device="cuda"),
+            torch.empty(B, dtype=torch.int32, device="cuda"))
+
+
+def _noalloc(mld, g, msg, llr, s, iters, early_term, outs=None):
     """One call through the C ABI with caller-owned device buffers."""
     B, n = llr.shape[0], g.n_vn
-    bits = torch.empty((B, n), dtype=torch.uint8, device="cuda")
-    post = torch.empty((B, n), dtype=torch.float32, device="cuda")
-    conv = torch.empty(B, dtype=torch.uint8, device="cuda")
-    used = torch.empty(B, dtype=torch.int32, device="cuda")
+    bits, post, conv, used = outs if outs is not None else _outputs(B, n)
     p = lambda t: ctypes.c_void_p(t.data_ptr())
     flags = mld.MLD_DEVICE_PTRS | (mld.MLD_EARLY_TERM if early_term else 0)
     dt = mld.MLD_MSG_F16 if msg == "f16" else mld.MLD_MSG_F32
@@ -67,6 +71,26 @@ def test_noalloc_matches_decoder_on_two_calls_in_a_row():
         assert np.array_equal(got["converged"], ref["converged"].cpu().numpy())
         assert np.array_equal(got["iters_used"], ref["iters_used"].cpu().numpy())
         np.testing.assert_allclose(got["post"], ref["post"].cpu().numpy(), rtol=0, atol=1e-6)
+
+
+def test_a_warm_call_takes_no_device_memory():
+    """After the first call on the device (which may load the library's
+    module and with it the static array), a call must leave the device's
+    free memory unchanged: the outputs are allocated beforehand by the
+    caller, and the library itself allocates nothing."""
+    import paper_1711_01783_gb300 as mld
+    g0 = preset_graph(0.1, 4096, 1)
+    g = mld.Graph.from_edges(g0)
+    w = make_workload(0.1, 4096, 40, 1, 4300, beta=0.40, graph=g0)
+    llr, s = _dev(_llr32(w)), _dev(w.s)
+    outs = _outputs(40, g.n_vn)
+    _noalloc(mld, g, "f16", llr, s, 10, True, outs)  # warm-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    got = _noalloc(mld, g, "f16", llr, s, 10, True, outs)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert got["iters_used"].max() <= 10
 
 
 def test_noalloc_refuses_a_working_set_larger_than_its_array():
