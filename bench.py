@@ -61,6 +61,9 @@ def parse():
                          "rates 0.1/0.05/0.02 and n in {2^16, 2^18, 10^6}, caps 100/150/200, early "
                          "termination, one captured plan")
     ap.add_argument("--tune-cache", default=None)
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the sub-records (FP32 storage; rates 0.05 and 0.02)")
+    ap.add_argument("--sub-steps", type=int, default=8)
     return ap.parse_args()
 
 
@@ -76,6 +79,22 @@ TIMING_EVERY = 10
 # grows with n, so it is scaled by the units a full pass processes.  Valid
 # for the kernel of this commit only (see profiles/).
 CHECK_PASS_TRAFFIC_PER_CW_BIT = {(0.1, "f16"): 397.17e6 / (64 * 3e5)}
+
+
+def algorithmic_bytes(st: dict, msg: str) -> tuple[float, float]:
+    """Minimum bytes per codeword of one check-update pass and of one whole
+    iteration, at message width b (2 for half storage, 4 for float):
+      check pass: r read and written on every core edge (2 b e_core), the
+        degree-1 channel terms read once (b m2), core posteriors read once
+        (4 n_core), syndrome bits (m / 8);
+      iteration: r read and written once (2 b e_core), degree-1 terms
+        (b m2), core VNs: channel term read, posterior written and read
+        (n_core (b + 8)), syndrome bits (m / 8)."""
+    b = 2 if msg == "f16" else 4
+    e, m2, nc, m = st["e_core"], st["n_deg1"], st["n_core"], st["n_cn"]
+    check = 2 * b * e + b * m2 + 4 * nc + m / 8
+    iteration = 2 * b * e + b * m2 + nc * (b + 8) + m / 8
+    return check, iteration
 
 
 def workload_config(a) -> dict:
@@ -381,6 +400,85 @@ def run_wbp(a, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def time_steps(step, steps: int, warmup: int, stream, barrier) -> float:
+    """Device time (ms) of `steps` calls after `warmup` untimed ones, bracketed
+    by a barrier and a synchronize on both sides."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def kernel_summary(kt: dict, st: dict, msg: str, batch: int, iters: int, steps: int, ms_step: float,
+                   peak: float) -> dict:
+    """Check-pass and whole-decode roofline fractions from the library's
+    per-iteration CUDA events (one timed region = one pass)."""
+    check_b, iter_b = algorithmic_bytes(st, msg)
+    check_ms = kt["check_ms"] / max(1, kt["check_timed"])
+    var_ms = kt["var_ms"] / max(1, kt["var_timed"])
+    achieved = check_b * batch / (check_ms * 1e-3) / 1e9
+    decode_gbs = iter_b * batch * iters / (ms_step * 1e-3) / 1e9
+    return {"achieved": achieved, "frac": achieved / peak, "pass_ms": check_ms, "var_update_ms": var_ms,
+            "algorithmic_bytes_per_pass": check_b * batch,
+            "algorithmic_bytes_per_iteration": iter_b * batch,
+            "decode_gbs": decode_gbs, "frac_decode": decode_gbs / peak,
+            "check_launches_per_pass": kt["check_launches"] / max(1, iters * steps),
+            "timed_passes": kt["check_timed"],
+            "share_check": check_ms * iters / max(1e-9, ms_step)}
+
+
+def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: float) -> dict:
+    """One more fixed-iteration workload measured like the headline (device-
+    resident inputs, CUDA events, max over ranks), with fewer steps."""
+    import torch
+    import paper_1711_01783_gb300 as mld
+    from synthetic import make_workload
+    iters = DEFAULT_ITERS[rate]
+    wl = make_workload(rate, a.n, a.batch, 2, rank_data_seed(rank), beta=a.beta)
+    g = mld.Graph.from_edges(wl.graph)
+    dec = mld.Decoder(g, a.batch, msg_dtype=msg)
+    y = torch.from_numpy(wl.y).to(dev)
+    sig = torch.from_numpy(wl.sigma).to(dev)
+    syn = torch.from_numpy(wl.s).to(dev)
+    out = dict(bits=torch.empty((a.batch, a.n), dtype=torch.uint8, device=dev), post=None,
+               converged=torch.empty(a.batch, dtype=torch.uint8, device=dev),
+               iters_used=torch.empty(a.batch, dtype=torch.int32, device=dev))
+    stream = torch.cuda.current_stream()
+    step = lambda: dec.decode_y(y, sig, syn, iters, out=out)  # noqa: E731
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    dec.timing(TIMING_EVERY)
+    dec.read_timing()
+    ms = time_steps(step, a.sub_steps, 0, stream, barrier)
+    dec.timing(0)
+    kt = dec.read_timing()
+    ms_max, launches = reduce_over_ranks(dist, ms, kt["check_launches"] + kt["var_launches"]
+                                         + kt["syndrome_launches"] + kt["layout_launches"], dev)
+    world = dist.get_world_size() if dist is not None else 1
+    ks = kernel_summary(kt, g.stats, msg, a.batch, iters, a.sub_steps, ms_max / a.sub_steps, peak)
+    conv = int(out["converged"].sum().item())
+    rec = {"value": job_throughput(world, a.batch, a.n, a.sub_steps, ms_max), "unit": UNIT,
+           "ms_per_step": ms_max / a.sub_steps, "steps": a.sub_steps, "warmup": 3,
+           "rate": rate, "iters": iters, "msg_storage": msg, "gpu_launches": launches,
+           "frames_converged": conv, "fer": 1.0 - conv / a.batch}
+    rec.update({k: ks[k] for k in ("frac", "frac_decode", "pass_ms", "var_update_ms", "share_check")})
+    dec.close()
+    g.close()
+    return rec
+
+
 def main():
     a = parse()
     if a.workload == "wbp":
@@ -455,23 +553,14 @@ def main():
     dec.timing(TIMING_EVERY)
     dec.read_timing()
     clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    ms = time_steps(step, a.steps, 0, stream, barrier)
     clk = clocks.stop()
     dec.timing(0)
     kt = dec.read_timing()
-    ms = e0.elapsed_time(e1)
     ms_max, launches = reduce_over_ranks(dist, ms, kt["check_launches"] + kt["var_launches"]
                                          + kt["syndrome_launches"] + kt["layout_launches"], dev)
     value = job_throughput(world, a.batch, a.n, a.steps, ms_max)
+    frames_converged = int(out["converged"].sum().item())
 
     # ---- end to end through the host-pointer path ---------------------------
     e2e = None
@@ -506,22 +595,26 @@ def main():
     # One check-update pass per iteration (one launch per check class); its
     # time is the sum of those launches, measured by the library's CUDA events
     # on the launching stream during the timed region.
-    b = 2 if a.msg == "f16" else 4
-    per_cw = 2 * b * st["e_core"] + 4 * st["n_core"] + 4 * st["n_deg1"] + st["n_cn"] / 8
-    check_ms = kt["check_ms"] / max(1, kt["check_timed"])      # one timed region = one pass
-    achieved = per_cw * a.batch / (check_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
+    ks = kernel_summary(kt, st, a.msg, a.batch, a.iters, a.steps, ms_max / a.steps, peak)
     tpb = CHECK_PASS_TRAFFIC_PER_CW_BIT.get((a.rate, a.msg))
-    var_ms = kt["var_ms"] / max(1, kt["var_timed"])
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": tpb * a.batch * a.n if tpb else None,
+    roofline = {"bound": "hbm", "achieved": ks["achieved"], "peak": peak, "unit": "GB/s",
+                "frac": ks["frac"], "traffic": tpb * a.batch * a.n if tpb else None,
                 "kernel": "k_check_update (one pass = all check classes of one iteration)",
-                "peak_kind": peak_kind, "pass_ms": check_ms,
-                "algorithmic_bytes_per_pass": per_cw * a.batch,
-                "check_launches_per_pass": kt["check_launches"] / max(1, a.iters * a.steps),
-                "timed_passes": kt["check_timed"],
-                "var_update_ms": var_ms,
-                "share_check": check_ms * a.iters * a.steps / max(1e-9, ms_max)}
+                "peak_kind": peak_kind}
+    roofline.update({k: v for k, v in ks.items() if k not in ("achieved", "frac")})
+    dec.close()
+    g.close()
+
+    # ---- sub-records: the same measurement on the other storage type and
+    # the other rates (fewer steps each) --------------------------------------
+    sub = {}
+    if not a.no_sub and a.n == 1_000_000 and a.batch == 64:
+        other = "f32" if a.msg == "f16" else "f16"
+        sub[f"rate{a.rate}_{other}"] = sub_record(a.rate, other, a, rank, dev, dist, barrier, peak)
+        for r in (0.1, 0.05, 0.02):
+            if r != a.rate:
+                sub[f"rate{r}_{a.msg}"] = sub_record(r, a.msg, a, rank, dev, dist, barrier, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -535,7 +628,8 @@ def main():
             "data": "synthetic (seeded MET ensemble, BIAWGN samples)", "config": workload_config(a),
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clk,
-            "frames_converged": int(out["converged"].sum().item()),
+            "frames_converged": frames_converged, "fer": 1.0 - frames_converged / a.batch,
+            "sub": sub,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
