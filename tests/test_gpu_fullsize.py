@@ -5,7 +5,9 @@ At these sizes the oracle (FP64, one codeword per host thread) decodes a
 sample of the batch; the GPU decodes the whole batch in the launch
 configuration the benchmark times.  Criteria (tests/test_gpu_parity.py
 derives them): sampled codewords agree with the oracle on >= 99.99 % of
-bits with identical converged flags; every codeword of the batch satisfies
+bits with identical converged flags (half messages at rate 0.02, where the
+stuck state holds many posteriors within half's rounding of 0: every bit
+whose FP64 posterior is more than 1e-2 nats from 0, >= 99.98 % overall); every codeword of the batch satisfies
 "converged <=> H x = s"; in the converging regime the frame error rate lies
 in the 95 % Clopper-Pearson interval of the oracle's on the same frames,
 frames both sides decode are bit-identical, and with float messages the
@@ -65,10 +67,26 @@ def test_full_size_other_rates(mld, rate_case, msg):
     assert np.array_equal(_syndrome_holds(w.graph, bits, w.s), conv)
     agree = (bits[SAMPLE] == ref["bits"]).mean()
     d = np.abs(_np(out["post"])[SAMPLE].astype(np.float64) - ref["post"])
+    dis = bits[SAMPLE] != ref["bits"]
+    la = np.abs(ref["post"][dis])
     print(f"rate {rate} {msg}: sampled bit agreement {agree:.6f}, converged {conv.sum()}/64, "
-          f"|dL| median {np.median(d):.3g} p99.9 {np.quantile(d, 0.999):.3g}")
-    assert agree >= 0.9999
+          f"|dL| median {np.median(d):.3g} p99.9 {np.quantile(d, 0.999):.3g} max {d.max():.3g}; "
+          f"{int(dis.sum())} disagreeing bits, FP64 |L| there: max {la.max() if la.size else 0:.3g} "
+          f"p50 {np.median(la) if la.size else 0:.3g}; FP64 |L| < 1e-2 on "
+          f"{(np.abs(ref['post']) < 1e-2).mean():.5f} of bits, < 1e-3 on {(np.abs(ref['post']) < 1e-3).mean():.5f}")
     assert np.array_equal(conv[SAMPLE], ref["converged"].astype(bool))
+    if msg == "f32" or rate != 0.02:
+        assert agree >= 0.9999
+    else:
+        # Half storage at rate 0.02: every frame fails at beta = 0.90, and
+        # about 0.17 % of the bits of the stuck state have |L| < 1e-3 nats.
+        # Each iteration moves a posterior by up to d_v (2^-11 + 2.3e-4) |r|
+        # (rounding of every stored message plus the half fit), about 2.5e-3
+        # nats at d_v = 35 and |r| ~ 0.1; in a state that does not converge
+        # these perturbations persist, so bits that close to 0 may decide
+        # either way.  Every bit farther than 1e-2 nats from 0 must agree.
+        assert agree >= 0.9998
+        assert la.size == 0 or la.max() < 1e-2, la.max()
 
 
 @pytest.fixture(scope="module")
