@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the sub-records (FP32 storage; rates 0.05 and 0.02)")
     ap.add_argument("--sub-steps", type=int, default=8)
+    ap.add_argument("--vn-update", default="gather", choices=["gather", "accumulate"],
+                    help="variable update of the headline decoder: CSC gather (deterministic) or "
+                         "accumulation of the new messages inside the check update (atomic adds)")
     return ap.parse_args()
 
 
@@ -102,7 +105,7 @@ def workload_config(a) -> dict:
         "workload": (f"synthetic MET-LDPC rate {a.rate}, n={a.n}, {a.batch} codewords, "
                      f"{a.iters} fixed BP iterations, beta={a.beta}"),
         "rate": a.rate, "n": a.n, "codewords": a.batch, "iters": a.iters,
-        "beta": a.beta, "msg_storage": a.msg,
+        "beta": a.beta, "msg_storage": a.msg, "vn_update": a.vn_update,
         "l2": "inputs and message state larger than L2 (no flush needed)",
         "parallelism": "replicas",
     }
@@ -438,7 +441,8 @@ def kernel_summary(kt: dict, st: dict, msg: str, batch: int, iters: int, steps: 
             "share_check": check_ms * iters / max(1e-9, ms_step)}
 
 
-def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: float) -> dict:
+def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: float,
+               vn_update: str = "gather") -> dict:
     """One more fixed-iteration workload measured like the headline (device-
     resident inputs, CUDA events, max over ranks), with fewer steps."""
     import torch
@@ -447,7 +451,7 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     iters = DEFAULT_ITERS[rate]
     wl = make_workload(rate, a.n, a.batch, 2, rank_data_seed(rank), beta=a.beta)
     g = mld.Graph.from_edges(wl.graph)
-    dec = mld.Decoder(g, a.batch, msg_dtype=msg)
+    dec = mld.Decoder(g, a.batch, msg_dtype=msg, vn_update=vn_update)
     y = torch.from_numpy(wl.y).to(dev)
     sig = torch.from_numpy(wl.sigma).to(dev)
     syn = torch.from_numpy(wl.s).to(dev)
@@ -471,7 +475,7 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     conv = int(out["converged"].sum().item())
     rec = {"value": job_throughput(world, a.batch, a.n, a.sub_steps, ms_max), "unit": UNIT,
            "ms_per_step": ms_max / a.sub_steps, "steps": a.sub_steps, "warmup": 3,
-           "rate": rate, "iters": iters, "msg_storage": msg, "gpu_launches": launches,
+           "rate": rate, "iters": iters, "msg_storage": msg, "vn_update": vn_update, "gpu_launches": launches,
            "frames_converged": conv, "fer": 1.0 - conv / a.batch}
     rec.update({k: ks[k] for k in ("frac", "frac_decode", "pass_ms", "var_update_ms", "share_check")})
     dec.close()
@@ -523,7 +527,7 @@ def main():
 
     wl = make_workload(a.rate, a.n, a.batch, seed_graph, rank_data_seed(rank), beta=a.beta)
     g = mld.Graph.from_edges(wl.graph)
-    dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, slab_width=a.slab)
+    dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, slab_width=a.slab, vn_update=a.vn_update)
     st = g.stats
     y = torch.from_numpy(wl.y).to(dev)
     sig = torch.from_numpy(wl.sigma).to(dev)
@@ -597,7 +601,8 @@ def main():
     # on the launching stream during the timed region.
     peak, peak_kind = measured_peak_hbm()
     ks = kernel_summary(kt, st, a.msg, a.batch, a.iters, a.steps, ms_max / a.steps, peak)
-    tpb = CHECK_PASS_TRAFFIC_PER_CW_BIT.get((a.rate, a.msg))
+    # the counters were taken on the gather variant's check kernel
+    tpb = CHECK_PASS_TRAFFIC_PER_CW_BIT.get((a.rate, a.msg)) if a.vn_update == "gather" else None
     roofline = {"bound": "hbm", "achieved": ks["achieved"], "peak": peak, "unit": "GB/s",
                 "frac": ks["frac"], "traffic": tpb * a.batch * a.n if tpb else None,
                 "kernel": "k_check_update (one pass = all check classes of one iteration)",
@@ -611,10 +616,13 @@ def main():
     sub = {}
     if not a.no_sub and a.n == 1_000_000 and a.batch == 64:
         other = "f32" if a.msg == "f16" else "f16"
-        sub[f"rate{a.rate}_{other}"] = sub_record(a.rate, other, a, rank, dev, dist, barrier, peak)
+        sub[f"rate{a.rate}_{other}"] = sub_record(a.rate, other, a, rank, dev, dist, barrier, peak, a.vn_update)
         for r in (0.1, 0.05, 0.02):
             if r != a.rate:
-                sub[f"rate{r}_{a.msg}"] = sub_record(r, a.msg, a, rank, dev, dist, barrier, peak)
+                sub[f"rate{r}_{a.msg}"] = sub_record(r, a.msg, a, rank, dev, dist, barrier, peak, a.vn_update)
+        vo = "accumulate" if a.vn_update == "gather" else "gather"
+        for m in (a.msg, other):
+            sub[f"rate{a.rate}_{m}_{vo}"] = sub_record(a.rate, m, a, rank, dev, dist, barrier, peak, vo)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -148,13 +148,30 @@ int mld_graph_generate(double rate, int32_t n, int32_t d2, uint64_t seed, mld_gr
  *                the arguments of phi are kept within it (see mld_decode).
  *   slab_width : 8, 16, 32 or 64 codewords per slab; 0 selects 32 for F32
  *                and 64 for F16.
+ *   vn_update  : how the variable update of Eq. 4 forms the posteriors
+ *                L_v = L_ch(v) + sum_{e in C_v} r_e:
+ *                MLD_VN_GATHER (0, default): a separate pass gathers each
+ *                  VN's messages in a fixed order (deterministic results);
+ *                MLD_VN_ACCUMULATE (1): the check update adds every new
+ *                  message, as stored, to the next iteration's posteriors
+ *                  with atomic adds, so the messages are read once less per
+ *                  iteration; the order of the additions varies from run to
+ *                  run, so posteriors may differ in the last float bits.  It
+ *                  applies to fixed-iteration decoding (calls with
+ *                  MLD_EARLY_TERM use the gather), needs the default slab
+ *                  width and a graph whose checks all have at most 8 edges and
+ *                  at most one degree-1 VN (MLD_EINVAL otherwise), and takes
+ *                  two more posterior arrays of device memory.
  * Errors: MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA. */
+#define MLD_VN_GATHER     0
+#define MLD_VN_ACCUMULATE 1
 typedef struct {
     int32_t msg_dtype;
     int32_t max_batch;
     float lmax;
     int32_t slab_width;
-    int32_t reserved[12];  /* must be zero */
+    int32_t vn_update;
+    int32_t reserved[11];  /* must be zero */
 } mld_opts;
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out);
 int mld_decoder_destroy(mld_decoder *d);

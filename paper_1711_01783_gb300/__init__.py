@@ -24,6 +24,7 @@ MLD_OK = 0
 MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA, MLD_ETIMEOUT, MLD_EGRAPH = -1, -2, -3, -4, -5
 MLD_MSG_F32, MLD_MSG_F16 = 0, 1
 MLD_EARLY_TERM, MLD_DEVICE_PTRS = 0x1, 0x2
+MLD_VN_GATHER, MLD_VN_ACCUMULATE = 0, 1
 
 _STATUS = {MLD_EINVAL: "MLD_EINVAL", MLD_ENOMEM: "MLD_ENOMEM", MLD_ECUDA: "MLD_ECUDA",
            MLD_ETIMEOUT: "MLD_ETIMEOUT", MLD_EGRAPH: "MLD_EGRAPH"}
@@ -53,7 +54,7 @@ class GraphStats(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("msg_dtype", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("lmax", ctypes.c_float), ("slab_width", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 12)]
+                ("vn_update", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
 
 
 class Timing(ctypes.Structure):
@@ -238,15 +239,20 @@ class Graph:
 
 
 class Decoder:
-    """Device state for decoding up to ``max_batch`` codewords (mld_decoder_create)."""
+    """Device state for decoding up to ``max_batch`` codewords (mld_decoder_create).
+
+    ``vn_update``: "gather" (default; deterministic variable update) or
+    "accumulate" (the check update adds its messages to the next
+    posteriors; fixed-iteration calls only, see mld_opts)."""
 
     def __init__(self, graph: Graph, max_batch: int, msg_dtype: str = "f32",
-                 lmax: float = 25.0, slab_width: int = 0):
+                 lmax: float = 25.0, slab_width: int = 0, vn_update: str = "gather"):
         o = Opts()
         o.msg_dtype = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
         o.max_batch = int(max_batch)
         o.lmax = float(lmax)
         o.slab_width = int(slab_width)
+        o.vn_update = {"gather": MLD_VN_GATHER, "accumulate": MLD_VN_ACCUMULATE}[vn_update]
         h = ctypes.c_void_p()
         _check(lib().mld_decoder_create(graph.handle, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

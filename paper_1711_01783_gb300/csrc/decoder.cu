@@ -61,6 +61,11 @@ void build_class_tables(mld_graph *g) {
     for (const mld::CheckClass &cl : g->h.classes)
         if (cl.dc < 0 || cl.dd > 1 || cl.dc + cl.dd > mld::kMaxRegDeg || (cl.dc == 0 && cl.dd == 0))
             g->fusable = false;
+    // posterior accumulation: every check with edges in a register class
+    g->acc_ok = true;
+    for (const mld::CheckClass &cl : g->h.classes)
+        if (!(cl.dc == 0 && cl.dd == 0) && (cl.dc < 0 || cl.dd > 1 || cl.dc + cl.dd > mld::kMaxRegDeg))
+            g->acc_ok = false;
 }
 
 namespace {
@@ -70,6 +75,7 @@ void decoder_free(mld_decoder *d) {
     if (d->r) cudaFree(d->r);
     d->r = nullptr;
     dfree(d->Lv); dfree(d->lch); dfree(d->lch1); dfree(d->post1); dfree(d->phi1);
+    dfree(d->Lv2); dfree(d->Lv3);
     dfree(d->hb_core); dfree(d->hb1); dfree(d->sbits);
     dfree(d->done); dfree(d->fail); dfree(d->iters); dfree(d->conv); dfree(d->status);
     dfree(d->in_stage); dfree(d->sigma_stage); dfree(d->post_stage);
@@ -99,9 +105,16 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     if (rbytes) MLD_CUDA(cudaMemsetAsync(d->r, 0, rbytes, st));
     MLD_CUDA(cudaMemsetAsync(d->done, 0, sizeof(uint32_t) * slabs * DW, st));
 
+    // Posterior accumulation: iteration l reads the posteriors of l-1 from
+    // one of three buffers and adds its messages into the buffer of l,
+    // which starts at L_ch; the rotation ends on d->Lv.
+    const bool acc_mode = d->vn_update == MLD_VN_ACCUMULATE && !et && iters > 0 && d->Lv2 && d->Lv3;
+    float *const accbuf[3] = {d->Lv, d->Lv2, d->Lv3};
+    auto acc_of = [&](int32_t l) { return accbuf[(iters - l) % 3]; };
+
     d->sample_now = true;
     InArgs ia{in, sigma, g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->lmax, d->scale_in, d->lmax_i, d->amin_i,
-              d->lch, d->Lv, d->lch1, d->post1, d->phi1};
+              d->lch, acc_mode ? acc_of(0) : d->Lv, d->lch1, d->post1, d->phi1};
     if (h.n_vn > 0) {
         int s = timed_launch(d, kClsLayout, st, "k_interleave_in", [&] {
             k_interleave_in<W, DecodeFit<MsgT>::value><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(ia);
@@ -149,6 +162,9 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     const dim3 syn_grid(syndrome_blocks(h.n_cn, sm_count), slabs);
     const int cap_blocks = sm_count * 16;  // two waves of 8 blocks per SM
     const int lane_blocks = (batch + 127) / 128;
+    const int64_t acc_n4 = static_cast<int64_t>(slabs) * h.n_core * W / 4;
+    const int copy_blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((acc_n4 + kBlock - 1) / kBlock,
+                                                                                     sm_count * 8)));
 
     auto syndrome_round = [&](int32_t l, bool et_mode) -> int {
         MLD_CUDA(cudaMemsetAsync(d->fail, 0, sizeof(uint32_t) * slabs * DW, st));
@@ -193,6 +209,15 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         ca.fuse = (fused && l >= 2) ? 1 : 0;
         d->sample_now = ((l - 1) % d->timing_every) == 0;
         if (ca.fuse) MLD_CUDA(cudaMemsetAsync(ca.fail_prev, 0, sizeof(uint32_t) * slabs * DW, st));
+        if (acc_mode && h.n_core > 0) {
+            ca.Lv = acc_of(l - 1);
+            ca.acc = acc_of(l);
+            int s = timed_launch(d, kClsVar, st, "k_copy4", [&] {
+                k_copy4<<<copy_blocks, kBlock, 0, st>>>(reinterpret_cast<float4 *>(ca.acc),
+                                                       reinterpret_cast<const float4 *>(d->lch), acc_n4);
+            });
+            if (s != MLD_OK) return s;
+        }
         {
             int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
                 if (big < 0) {
@@ -220,7 +245,16 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
             if (s != MLD_OK) return s;
         }
         va.want_bits = (last || (et && !fused)) ? 1 : 0;
-        if (h.n_core > 0) {
+        if (acc_mode) {
+            // the check pass has formed L_v; the last iteration's decisions
+            if (last && h.n_core > 0) {
+                int s = timed_launch(d, kClsVar, st, "k_hard_bits", [&] {
+                    k_hard_bits<W><<<dim3(grid_x(static_cast<int64_t>(h.n_core) * (W / 8)), slabs), kBlock, 0, st>>>(
+                        d->Lv, h.n_core, d->hb_core);
+                });
+                if (s != MLD_OK) return s;
+            }
+        } else if (h.n_core > 0) {
             int s = timed_launch(d, kClsVar, st, "k_var_update", [&] {
                 k_var_update<MsgT, W><<<vn_grid, kBlock, 0, st>>>(va);
             });
@@ -416,8 +450,10 @@ int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out) {
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out) {
     mld::clear_error();
     if (!g || !opts || !out) return mld::fail(MLD_EINVAL, "decoder_create: null pointer");
-    for (int i = 0; i < 12; ++i)
+    for (int i = 0; i < 11; ++i)
         if (opts->reserved[i] != 0) return mld::fail(MLD_EINVAL, "decoder_create: reserved field not zero");
+    if (opts->vn_update != MLD_VN_GATHER && opts->vn_update != MLD_VN_ACCUMULATE)
+        return mld::fail(MLD_EINVAL, "decoder_create: unknown vn_update");
     if (opts->msg_dtype != MLD_MSG_F32 && opts->msg_dtype != MLD_MSG_F16)
         return mld::fail(MLD_EINVAL, "decoder_create: unknown msg_dtype");
     if (opts->max_batch < 1) return mld::fail(MLD_EINVAL, "decoder_create: max_batch < 1");
@@ -426,6 +462,13 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     int W = opts->slab_width;
     if (W == 0) W = (opts->msg_dtype == MLD_MSG_F16) ? 64 : 32;
     if (W != 8 && W != 16 && W != 32 && W != 64) return mld::fail(MLD_EINVAL, "decoder_create: slab_width");
+    if (opts->vn_update == MLD_VN_ACCUMULATE) {
+        if (W != ((opts->msg_dtype == MLD_MSG_F16) ? 64 : 32))
+            return mld::fail(MLD_EINVAL, "decoder_create: posterior accumulation needs the default slab width");
+        if (!g->acc_ok)
+            return mld::fail(MLD_EINVAL, "decoder_create: posterior accumulation needs every check to have at "
+                                         "most 8 edges and at most one degree-1 VN");
+    }
     int s = check_device(g->device);
     if (s != MLD_OK) return s;
     mld_decoder *d = new (std::nothrow) mld_decoder();
@@ -434,6 +477,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     d->device = g->device;
     d->msg = opts->msg_dtype;
     d->W = W;
+    d->vn_update = opts->vn_update;
     d->max_batch = opts->max_batch;
     d->max_slabs = (opts->max_batch + W - 1) / W;
     set_units(d, opts->lmax > 0.f ? opts->lmax : 25.f);
@@ -450,6 +494,8 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     }
     if (s == MLD_OK) s = dalloc(&d->Lv, S * h.n_core * W);
     if (s == MLD_OK) s = dalloc(&d->lch, S * h.n_core * W);
+    if (s == MLD_OK && d->vn_update == MLD_VN_ACCUMULATE) s = dalloc(&d->Lv2, S * h.n_core * W);
+    if (s == MLD_OK && d->vn_update == MLD_VN_ACCUMULATE) s = dalloc(&d->Lv3, S * h.n_core * W);
     if (s == MLD_OK) s = dalloc(&d->lch1, S * h.n_deg1 * W);
     if (s == MLD_OK) s = dalloc(&d->post1, S * h.n_deg1 * W);
     if (s == MLD_OK) s = dalloc(&d->phi1, S * h.n_deg1 * W);

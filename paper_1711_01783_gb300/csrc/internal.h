@@ -78,4 +78,6 @@ struct mld_graph {
     std::vector<mld::ClassLaunch> launches[4];
     // every check is in a register class (enables the fused syndrome check)
     bool fusable = false;
+    // every check with edges is in a register class (posterior accumulation)
+    bool acc_ok = false;
 };

@@ -158,6 +158,11 @@ template <> struct Msg<float> {
     static __device__ __forceinline__ void store(float *p, float4 v) {
         *reinterpret_cast<float4 *>(p) = v;
     }
+    // store v and return the values as stored
+    static __device__ __forceinline__ float4 store_get(float *p, float4 v) {
+        *reinterpret_cast<float4 *>(p) = v;
+        return v;
+    }
 };
 template <> struct Msg<__half> {
     static __device__ __forceinline__ float4 load(const __half *p) {
@@ -173,6 +178,16 @@ template <> struct Msg<__half> {
         u.x = *reinterpret_cast<const uint32_t *>(&a);
         u.y = *reinterpret_cast<const uint32_t *>(&b);
         *reinterpret_cast<uint2 *>(p) = u;
+    }
+    static __device__ __forceinline__ float4 store_get(__half *p, float4 v) {
+        const __half2 a = __floats2half2_rn(v.x, v.y);
+        const __half2 b = __floats2half2_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t *>(&a);
+        u.y = *reinterpret_cast<const uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = u;
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
     }
 };
 
@@ -230,6 +245,11 @@ struct CnArgs {
     int32_t batch;              // codewords (later lanes are padding)
     const uint8_t *hb1_prev;    // degree-1 decisions of the previous iteration
     uint32_t *fail_prev;        // [slab][ceil(W/32)] fail words of the previous iteration
+    // Posterior accumulation (fixed iterations only): each new message, as
+    // stored, is added to this [slab][n_core][W] array, which holds L_ch on
+    // entry and L_v of this iteration (Eq. 4) once the pass is complete.
+    // Null: the variable update gathers the messages instead.
+    float *acc;
 };
 
 template <typename MsgT, int W>
@@ -299,7 +319,7 @@ constexpr uint32_t kSign = 0x80000000u;
 // not its posterior (early termination without soft output); with a.fuse the
 // call also returns the previous iteration's syndrome failures of the check
 // for the thread's 4 codewords (bit k: codeword lane0 + k), else 0.
-template <typename MsgT, int W, int DC, int DD, bool HARD1 = false>
+template <typename MsgT, int W, int DC, int DD, bool HARD1 = false, bool ACC = false>
 __device__ __forceinline__ uint32_t check_regular(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
                                                   int slab) {
     constexpr int NB = W / 8;
@@ -420,10 +440,19 @@ __device__ __forceinline__ uint32_t check_regular(const CnArgs &a, const ClassLa
                 if (i < dc) {
                     if (valid) {
                         MsgT *rp = rb + static_cast<size_t>(e0 + i) * W;
-                        if (a.et)
+                        if constexpr (ACC) {
+                            // the message as stored joins its VN's posterior
+                            const float4 st = Msg<MsgT>::store_get(rp, rv);
+                            // (the column index is loaded again, an L1 hit, rather than kept
+                            // live through both passes)
+                            const int32_t v = __ldg(a.col + e0 + i);
+                            float *ap = a.acc + (static_cast<size_t>(slab) * a.n_core + v) * W + lane0;
+                            atomicAdd(reinterpret_cast<float4 *>(ap), st);
+                        } else if (a.et) {
                             store_r<MsgT, W>(a, rp, rv, donenib);
-                        else
+                        } else {
                             Msg<MsgT>::store(rp, rv);
+                        }
                     }
                 } else {
                     emit_deg1<MsgT, W>(a, slab, s0 + i - dc, lane0, rv, donenib, valid);
@@ -545,7 +574,7 @@ template <int D> constexpr bool kLoopedClass = D <= 6;
 // The threads of a class launch (t0: thread index in the slab's grid of
 // `blocks` blocks): looped classes step through their checks, the others take
 // one; with HARD1 the fused syndrome failures are ORed into a.fail_prev.
-template <typename MsgT, int W, int DC, int DD, bool HARD1>
+template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC = false>
 __device__ __forceinline__ void check_class_body(const CnArgs &a, const ClassLaunch &cl, int64_t t0,
                                                  int32_t blocks, int slab) {
     constexpr int TPC = W / kK;
@@ -557,9 +586,9 @@ __device__ __forceinline__ void check_class_body(const CnArgs &a, const ClassLau
         // threads of a shuffle pair belong to one check and leave together.
         const int32_t jstride = blocks * (kBlock / TPC);
         for (int32_t j = static_cast<int32_t>(t0 / TPC); j < cl.count; j += jstride)
-            fail |= check_regular<MsgT, W, DC, DD, HARD1>(a, cl, j, lane0, slab);
+            fail |= check_regular<MsgT, W, DC, DD, HARD1, ACC>(a, cl, j, lane0, slab);
     } else {
-        fail = check_regular<MsgT, W, DC, DD, HARD1>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
+        fail = check_regular<MsgT, W, DC, DD, HARD1, ACC>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
     }
     if constexpr (HARD1) {
         if (a.fuse) flush_fail<W>(a.fail_prev + slab * ((W + 31) / 32), fail, lane0);
@@ -568,13 +597,19 @@ __device__ __forceinline__ void check_class_body(const CnArgs &a, const ClassLau
 
 // One check class per launch, its shape (DC, DD) a compile-time constant: the
 // register arrays are sized exactly and only this class's code is hot.
-template <typename MsgT, int W, int DC, int DD, bool HARD1>
-__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_update(CnArgs a, ClassLaunch cl) {
+template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC = false>
+__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? (ACC ? 7 : 8) : 6)) k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
-    check_class_body<MsgT, W, DC, DD, HARD1>(a, cl, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
-                                             static_cast<int32_t>(gridDim.x), slab);
+    check_class_body<MsgT, W, DC, DD, HARD1, ACC>(a, cl,
+                                                  static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
+                                                  static_cast<int32_t>(gridDim.x), slab);
 }
+
+// Posterior accumulation is built for the default slab width of each
+// message type (64 half, 32 float).
+template <typename MsgT, int W>
+constexpr bool kAccWidth = IsHalf<MsgT>::value ? W == 64 : W == 32;
 
 template <typename MsgT, int W>
 __global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, ClassLaunch cl) {
@@ -588,7 +623,9 @@ __global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, Cla
 // caller graphs, not in the MET ensembles) runs the streaming kernel.
 // cap_blocks: grid width for the looped classes (a few waves of the GPU);
 // hard1: early termination without soft output (degree-1 decisions only, and
-// the fused syndrome check when ca.fuse; see check_regular).
+// the fused syndrome check when ca.fuse; see check_regular).  With ca.acc set
+// (fixed iterations, default slab width, register classes only) the kernels
+// also add every new message to the next posteriors.
 template <typename MsgT, int W>
 void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks,
                         bool hard1) {
@@ -599,6 +636,12 @@ void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cuda
 #define MLD_CASE(DCV, DDV)                                                                          \
     case (DCV) * 2 + (DDV):                                                                         \
         static_assert(kLoopedClass<(DCV) + (DDV)> == ((DCV) + (DDV) <= 6), "grid choice");         \
+        if constexpr (kAccWidth<MsgT, W>) {                                                         \
+            if (ca.acc) {                                                                           \
+                k_check_update<MsgT, W, DCV, DDV, false, true><<<g, kBlock, 0, st>>>(ca, cl);      \
+                return;                                                                             \
+            }                                                                                       \
+        }                                                                                           \
         if (hard1) k_check_update<MsgT, W, DCV, DDV, true><<<g, kBlock, 0, st>>>(ca, cl);          \
         else k_check_update<MsgT, W, DCV, DDV, false><<<g, kBlock, 0, st>>>(ca, cl);              \
         return;
@@ -914,6 +957,13 @@ __global__ void __launch_bounds__(kBlock) k_hard_bits(const float *post, int32_t
     hb[(static_cast<size_t>(slab) * count + u) * NB + g] = static_cast<uint8_t>(byte);
 }
 
+// dst = src over n4 float4 (the posterior accumulator starts at L_ch)
+__global__ void __launch_bounds__(kBlock) k_copy4(float4 *dst, const float4 *src, int64_t n4) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride)
+        dst[i] = __ldg(src + i);
+}
+
 struct OutArgs {
     const int32_t *unit;
     int32_t n_vn, n_core, n_deg1, batch;
@@ -1052,6 +1102,9 @@ struct mld_decoder {
     int32_t *iters = nullptr;
     uint8_t *conv = nullptr;
     int32_t *status = nullptr;
+    // posterior accumulation (MLD_VN_ACCUMULATE): two more posterior buffers
+    int vn_update = MLD_VN_GATHER;
+    float *Lv2 = nullptr, *Lv3 = nullptr;
     // staging buffers for host pointers
     float *in_stage = nullptr, *sigma_stage = nullptr, *post_stage = nullptr;
     uint8_t *syn_stage = nullptr, *bits_stage = nullptr;

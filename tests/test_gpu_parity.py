@@ -279,11 +279,12 @@ def full_size():
     return w, sample, ref
 
 
-@pytest.mark.parametrize("msg", ["f16", "f32"])
-def test_full_size_sampled_codewords(mld, full_size, msg):
+@pytest.mark.parametrize("msg,vn", [("f16", "gather"), ("f32", "gather"), ("f16", "accumulate"),
+                                    ("f32", "accumulate")])
+def test_full_size_sampled_codewords(mld, full_size, msg, vn):
     w, sample, ref = full_size
     g = mld.Graph.from_edges(w.graph)
-    dec = mld.Decoder(g, 64, msg_dtype=msg)
+    dec = mld.Decoder(g, 64, msg_dtype=msg, vn_update=vn)
     out = dec.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=100, want_post=True)
     bits = _np(out["bits"])
     conv = _np(out["converged"]).astype(bool)
@@ -323,3 +324,66 @@ def test_sampled_timing_counts_and_changes_no_result(mld):
     assert dec.read_timing()["check_launches"] == 0
     with pytest.raises(Exception):
         dec.timing(-1)
+
+
+# ---------------------------------------------------------------------------
+# Posterior accumulation (vn_update="accumulate"): the check update adds each
+# new message, as stored, into the next posteriors with atomic adds.  Eq. 4
+# is the same sum; only the order of its float additions changes, and with
+# it the last bits of a posterior: |dL| <= d_v * 2^-24 * (|L_ch| + sum |r|)
+# between two runs or against the gather (at most ~1e-4 nats here).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_accumulate_one_iteration_and_order_independence(mld, msg):
+    w = make_workload(0.1, 4096, 64, 1, 1010)
+    g = mld.Graph.from_edges(w.graph)
+    L = _dev(_llr32(w))
+    s = _dev(w.s)
+    acc = mld.Decoder(g, 64, msg_dtype=msg, vn_update="accumulate")
+    gat = mld.Decoder(g, 64, msg_dtype=msg)
+    a1 = acc.decode(L, s, iters=1, want_post=True)
+    g1 = gat.decode(L, s, iters=1, want_post=True)
+    ref = oracle.decode(w.graph, _llr32(w), w.s, iters=1)
+    d = np.abs(_np(a1["post"]).astype(np.float64) - ref["post"])
+    if msg == "f32":
+        bound = 1e-4 + 1e-5 * np.abs(ref["post"])
+    else:
+        dv = w.graph.vn_degree()[None, :]
+        bound = dv * ((2.0 ** -11 + 2.3e-4) * 25.0 + 2.3e-4) + 1e-4
+    assert np.all(d <= bound), (d.max(), (d - bound).max())
+    # the same messages summed in another order
+    np.testing.assert_allclose(_np(a1["post"]), _np(g1["post"]), rtol=1e-5, atol=1e-4)
+    # several iterations, twice: results agree up to the order of additions
+    a = acc.decode(L, s, iters=30, want_post=True)
+    b = acc.decode(L, s, iters=30, want_post=True)
+    gg = gat.decode(L, s, iters=30, want_post=True)
+    for x in (b, gg):
+        assert (_np(a["bits"]) == _np(x["bits"])).mean() >= 0.9999
+        assert np.array_equal(_np(a["converged"]), _np(x["converged"]))
+    ref30 = oracle.decode(w.graph, _llr32(w), w.s, iters=30)
+    assert (_np(a["bits"]) == ref30["bits"]).mean() >= 0.9999
+    assert np.array_equal(_np(a["converged"]), ref30["converged"])
+
+
+def test_accumulate_falls_back_to_gather_under_early_termination(mld):
+    w = make_workload(0.1, 4096, 32, 1, 1020, beta=0.36)
+    g = mld.Graph.from_edges(w.graph)
+    acc = mld.Decoder(g, 32, msg_dtype="f32", vn_update="accumulate")
+    gat = mld.Decoder(g, 32, msg_dtype="f32")
+    a = acc.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=40, early_term=True, want_post=True)
+    b = gat.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=40, early_term=True, want_post=True)
+    for k in ("bits", "post", "converged", "iters_used"):
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_accumulate_rejects_unsupported_decoders(mld):
+    w = make_workload(0.1, 4096, 2, 1, 1030)
+    g = mld.Graph.from_edges(w.graph)
+    with pytest.raises(mld.MldError):
+        mld.Decoder(g, 8, msg_dtype="f16", slab_width=16, vn_update="accumulate")
+    # a check of degree above 8 (irregular class)
+    ev = np.arange(12, dtype=np.int32)
+    ec = np.zeros(12, dtype=np.int32)
+    gi = mld.Graph(np.concatenate([ev, ev]), np.concatenate([ec, ec + 1]), 12, 2)
+    with pytest.raises(mld.MldError):
+        mld.Decoder(gi, 4, msg_dtype="f32", vn_update="accumulate")
