@@ -8,6 +8,12 @@ The arithmetic lives in ``oracle.c`` (plain C, FP64, one codeword per
 thread); see that file's header for the paper passages it follows and the
 readings it takes.  This module compiles it with gcc and wraps it with ctypes.
 
+Layered schedule (``decode_layered``): the same check and variable updates
+with the checks taken one at a time in a given order.  Pinned by MAP on
+cycle-free graphs, the one-sweep closed form of a repetition chain, the
+order-invariance of checks that share no VN, the coset symmetry, exhaustive
+ML and the noiseless limit (``tests/test_oracle_layered.py``).
+
 Weighted BP (``wbp``): forward plus a hand-written reverse-mode gradient,
 pinned by central finite differences of its own FP64 loss and by the
 all-weights-one case equalling plain BP.
@@ -64,6 +70,9 @@ def _load():
             lib.oracle_decode.restype = ctypes.c_int
             lib.oracle_decode.argtypes = [i32, i32, i64, ptr, ptr, i32, ptr, ptr,
                                           i32, i32, dbl, ptr, ptr, ptr, ptr, i32]
+            lib.oracle_decode_layered.restype = ctypes.c_int
+            lib.oracle_decode_layered.argtypes = [i32, i32, i64, ptr, ptr, ptr, i32, ptr, ptr,
+                                                  i32, i32, dbl, ptr, ptr, ptr, ptr, i32]
             lib.oracle_wbp.restype = ctypes.c_int
             lib.oracle_wbp.argtypes = [i32, i32, i64, ptr, ptr, ptr, i32, i32, ptr, ptr, ptr, i32, ptr, dbl,
                                        ptr, ptr, ptr, ptr, i32]
@@ -124,6 +133,31 @@ def decode(graph, llr: np.ndarray, syndrome: np.ndarray, iters: int,
                                int(threads or default_threads()))
     if st != 0:
         raise RuntimeError(f"oracle_decode failed with status {st}")
+    return dict(post=post, bits=bits, converged=conv, iters_used=used)
+
+
+def decode_layered(graph, llr: np.ndarray, syndrome: np.ndarray, iters: int, order,
+                   early_term: bool = False, lmax: float = LMAX, threads: int | None = None):
+    """Sum-product BP in FP64 with the layered (serial) schedule: the checks
+    are updated one at a time in ``order`` (every check once), each from the
+    latest messages.  Same inputs and outputs as :func:`decode`."""
+    n, m, ev, ec = _edges(graph)
+    L = np.ascontiguousarray(np.atleast_2d(llr), dtype=np.float64)
+    S = np.ascontiguousarray(np.atleast_2d(syndrome), dtype=np.uint8)
+    od = np.ascontiguousarray(order, dtype=np.int32)
+    B = L.shape[0]
+    if L.shape != (B, n) or S.shape != (B, m) or od.shape != (m,):
+        raise ValueError("shape mismatch")
+    post = np.zeros((B, n), dtype=np.float64)
+    bits = np.zeros((B, n), dtype=np.uint8)
+    conv = np.zeros(B, dtype=np.uint8)
+    used = np.zeros(B, dtype=np.int32)
+    st = _load().oracle_decode_layered(n, m, ev.shape[0], _p(ev), _p(ec), _p(od), B, _p(L), _p(S),
+                                       int(iters), int(bool(early_term)), float(lmax),
+                                       _p(post), _p(bits), _p(conv), _p(used),
+                                       int(threads or default_threads()))
+    if st != 0:
+        raise RuntimeError(f"oracle_decode_layered failed with status {st}")
     return dict(post=post, bits=bits, converged=conv, iters_used=used)
 
 

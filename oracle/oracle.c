@@ -131,6 +131,7 @@ typedef struct {
     int32_t *iters_used;     /* [batch] */
     int next;                /* work counter (atomic) */
     int status;
+    const int32_t *order;    /* layered schedule: the check order [n_cn] */
 } decode_job;
 
 static int decode_one(const decode_job *J, int b) {
@@ -248,8 +249,136 @@ int oracle_decode(int32_t n_vn, int32_t n_cn, int64_t n_edges,
     int st = adj_build(&a, n_vn, n_cn, n_edges, edge_vn, edge_cn);
     if (st != ORACLE_OK) return st;
     decode_job J = {&a, llr, syndrome, batch, max_iters, early_term, lmax,
-                    post, bits, converged, iters_used, 0, ORACLE_OK};
+                    post, bits, converged, iters_used, 0, ORACLE_OK, NULL};
     st = run_workers(decode_worker, &J, n_threads, batch);
+    adj_free(&a);
+    return st != ORACLE_OK ? st : J.status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Layered (serial) schedule, one codeword.                                   */
+/*                                                                           */
+/* The checks are updated one at a time in the order `order`; each check      */
+/* forms its incoming messages from the latest outgoing messages of the other */
+/* checks (those already updated in this iteration included), then replaces   */
+/* its own outgoing messages.  For check c, in order:                         */
+/*   q_{v->c} = clamp( Lch(v) + sum_{c' in C_v \ c} r_{c'->v} )  (Eq. 4)      */
+/*   r_{c->v} = clamp( (1-2 s_c) prod_{v' in R_c \ v} sgn q_{v'->c}           */
+/*                     * phi( sum_{v' in R_c \ v} phi(|q_{v'->c}|) ) )        */
+/*                                                            (Eqs. 2-3)     */
+/* with the clamps and readings of the flooding decoder above.  After every  */
+/* check has been updated once (one iteration), the posterior and decision   */
+/* of Eq. 5 and the syndrome comparison of Step 5 follow as in flooding.     */
+/* The schedule is not in the paper, which runs the flooding schedule of     */
+/* Steps 3-4; it reorders the same Steps 3-4 per check.                      */
+/* ------------------------------------------------------------------------- */
+static int decode_one_layered(const decode_job *J, int b) {
+    const adjacency *a = J->a;
+    const int32_t n = a->n_vn;
+    const int64_t E = a->n_edges;
+    const double lmax = J->lmax;
+    const double amin = oracle_phi(lmax);
+    const double *llr = J->llr + (size_t)b * n;
+    const uint8_t *s = J->syn + (size_t)b * a->n_cn;
+    double *Lch = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *L = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *q = malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    double *r = malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    double *phiq = malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    uint8_t *xhat = malloc((size_t)(n > 0 ? n : 1));
+    if (!Lch || !L || !q || !r || !phiq || !xhat) {
+        free(Lch); free(L); free(q); free(r); free(phiq); free(xhat);
+        return ORACLE_ENOMEM;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        Lch[v] = clampd(llr[v], -lmax, lmax);
+        L[v] = Lch[v];
+        xhat[v] = L[v] < 0.0;
+    }
+    for (int64_t e = 0; e < E; ++e) r[e] = 0.0;
+
+    int used = 0, conv = 0;
+    for (int l = 1; l <= J->max_iters; ++l) {
+        for (int32_t k = 0; k < a->n_cn; ++k) {
+            const int32_t c = J->order[k];
+            /* Eq. 4 for the edges of c, from the current messages */
+            for (int64_t k1 = a->cptr[c]; k1 < a->cptr[c + 1]; ++k1) {
+                const int64_t e = a->cedge[k1];
+                const int32_t v = a->edge_vn[e];
+                double acc = Lch[v];
+                for (int64_t k2 = a->vptr[v]; k2 < a->vptr[v + 1]; ++k2)
+                    if (a->vedge[k2] != e) acc += r[a->vedge[k2]];
+                q[e] = clampd(acc, -lmax, lmax);
+                phiq[e] = oracle_phi(clampd(fabs(q[e]), amin, lmax));
+            }
+            /* Eqs. 2-3 with the syndrome sign for the edges of c */
+            for (int64_t k1 = a->cptr[c]; k1 < a->cptr[c + 1]; ++k1) {
+                double sgn = (s[c] & 1) ? -1.0 : 1.0;
+                double sum = 0.0;
+                for (int64_t k2 = a->cptr[c]; k2 < a->cptr[c + 1]; ++k2) {
+                    if (k2 == k1) continue;
+                    const int64_t e2 = a->cedge[k2];
+                    if (q[e2] < 0.0) sgn = -sgn;
+                    sum += phiq[e2];
+                }
+                r[a->cedge[k1]] = clampd(sgn * oracle_phi(clampd(sum, amin, lmax)), -lmax, lmax);
+            }
+        }
+        /* Eq. 5: posterior and hard decision */
+        for (int32_t v = 0; v < n; ++v) {
+            double acc = Lch[v];
+            for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) acc += r[a->vedge[k]];
+            L[v] = acc;
+            xhat[v] = acc < 0.0;
+        }
+        used = l;
+        if (J->early_term && syndrome_ok(a, xhat, s)) { conv = 1; break; }
+    }
+    if (!conv) conv = syndrome_ok(a, xhat, s);
+    if (J->post) memcpy(J->post + (size_t)b * n, L, sizeof(double) * (size_t)n);
+    memcpy(J->bits + (size_t)b * n, xhat, (size_t)n);
+    J->converged[b] = (uint8_t)conv;
+    J->iters_used[b] = used;
+    free(Lch); free(L); free(q); free(r); free(phiq); free(xhat);
+    return ORACLE_OK;
+}
+
+static void *decode_layered_worker(void *arg) {
+    decode_job *J = arg;
+    for (;;) {
+        int b = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (b >= J->batch) break;
+        int st = decode_one_layered(J, b);
+        if (st != ORACLE_OK) __atomic_store_n(&J->status, st, __ATOMIC_RELAXED);
+    }
+    return NULL;
+}
+
+/* Layered decoding; `order` lists every check exactly once. */
+int oracle_decode_layered(int32_t n_vn, int32_t n_cn, int64_t n_edges,
+                          const int32_t *edge_vn, const int32_t *edge_cn, const int32_t *order,
+                          int32_t batch, const double *llr, const uint8_t *syndrome,
+                          int32_t max_iters, int32_t early_term, double lmax,
+                          double *post, uint8_t *bits, uint8_t *converged,
+                          int32_t *iters_used, int32_t n_threads) {
+    if (n_vn < 0 || n_cn < 0 || n_edges < 0 || batch < 0 || max_iters < 0 || !(lmax > 0.0))
+        return ORACLE_EINVAL;
+    if (batch == 0) return ORACLE_OK;
+    if (!llr || !syndrome || !bits || !converged || !iters_used || (n_cn > 0 && !order))
+        return ORACLE_EINVAL;
+    uint8_t *seen = calloc((size_t)n_cn + 1, 1);
+    if (!seen) return ORACLE_ENOMEM;
+    for (int32_t k = 0; k < n_cn; ++k) {
+        if (order[k] < 0 || order[k] >= n_cn || seen[order[k]]) { free(seen); return ORACLE_EINVAL; }
+        seen[order[k]] = 1;
+    }
+    free(seen);
+    adjacency a;
+    int st = adj_build(&a, n_vn, n_cn, n_edges, edge_vn, edge_cn);
+    if (st != ORACLE_OK) return st;
+    decode_job J = {&a, llr, syndrome, batch, max_iters, early_term, lmax,
+                    post, bits, converged, iters_used, 0, ORACLE_OK, order};
+    st = run_workers(decode_layered_worker, &J, n_threads, batch);
     adj_free(&a);
     return st != ORACLE_OK ? st : J.status;
 }

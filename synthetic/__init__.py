@@ -12,14 +12,19 @@ the workload the decoder is given.
   ``s = H x`` (the sender's side of the protocol, Step 1 of the paper's
   Methods), and Alice's binary-input AWGN observation ``y = (1-2x) + sigma*z``,
   with ``sigma`` solved from a target reconciliation efficiency ``beta``.
+* :mod:`synthetic.layers` -- a grouping of the checks into layers of checks
+  that share no VN of degree >= 2, which fixes the check order of the layered
+  (serial) schedule.
 """
 from .ensemble import MetGraph, met_ensemble, RATE_PRESETS, preset_graph
 from .channel import (biawgn_capacity, awgn_capacity, sigma_for_beta,
                       random_bits, bob_syndrome, biawgn_observe, Workload,
                       make_workload, make_uneven_workload)
+from .layers import check_layers, layer_order
 
 __all__ = [
     "MetGraph", "met_ensemble", "RATE_PRESETS", "preset_graph",
     "biawgn_capacity", "awgn_capacity", "sigma_for_beta", "random_bits",
     "bob_syndrome", "biawgn_observe", "Workload", "make_workload", "make_uneven_workload",
+    "check_layers", "layer_order",
 ]
