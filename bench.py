@@ -442,7 +442,7 @@ def kernel_summary(kt: dict, st: dict, msg: str, batch: int, iters: int, steps: 
 
 
 def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: float,
-               vn_update: str = "gather") -> dict:
+               vn_update: str = "gather", schedule: str = "flooding") -> dict:
     """One more fixed-iteration workload measured like the headline (device-
     resident inputs, CUDA events, max over ranks), with fewer steps."""
     import torch
@@ -451,7 +451,9 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     iters = DEFAULT_ITERS[rate]
     wl = make_workload(rate, a.n, a.batch, 2, rank_data_seed(rank), beta=a.beta)
     g = mld.Graph.from_edges(wl.graph)
-    dec = mld.Decoder(g, a.batch, msg_dtype=msg, vn_update=vn_update)
+    if schedule == "layered":
+        g.set_layers(None)
+    dec = mld.Decoder(g, a.batch, msg_dtype=msg, vn_update=vn_update, schedule=schedule)
     y = torch.from_numpy(wl.y).to(dev)
     sig = torch.from_numpy(wl.sigma).to(dev)
     syn = torch.from_numpy(wl.s).to(dev)
@@ -475,12 +477,54 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     conv = int(out["converged"].sum().item())
     rec = {"value": job_throughput(world, a.batch, a.n, a.sub_steps, ms_max), "unit": UNIT,
            "ms_per_step": ms_max / a.sub_steps, "steps": a.sub_steps, "warmup": 3,
-           "rate": rate, "iters": iters, "msg_storage": msg, "vn_update": vn_update, "gpu_launches": launches,
+           "rate": rate, "iters": iters, "msg_storage": msg, "vn_update": vn_update, "schedule": schedule,
+           "gpu_launches": launches,
            "frames_converged": conv, "fer": 1.0 - conv / a.batch}
     rec.update({k: ks[k] for k in ("frac", "frac_decode", "pass_ms", "var_update_ms", "share_check")})
     dec.close()
     g.close()
     return rec
+
+
+def schedule_comparison(a, dev, barrier, betas=(0.40, 0.42), cap: int = 100, steps: int = 5) -> dict:
+    """Flooding against the layered schedule where frames converge: rate 0.1,
+    n = 10^6, 64 codewords, early termination with a cap of 100 iterations.
+    Per (beta, schedule): decode time, decoded Mbit/s, mean iterations, FER."""
+    import torch
+    import paper_1711_01783_gb300 as mld
+    from synthetic import make_workload, preset_graph
+    graph = preset_graph(0.1, a.n, 2)
+    g = mld.Graph.from_edges(graph)
+    g.set_layers(None)
+    n_layers = g.layers()[1]
+    stream = torch.cuda.current_stream()
+    res = {"workload": f"rate 0.1, n={a.n}, {a.batch} codewords, early termination, cap {cap}, "
+                       f"{a.msg} messages; layered: the library's default layering ({n_layers} layers)"}
+    for beta in betas:
+        wl = make_workload(0.1, a.n, a.batch, 2, 7000, beta=beta, graph=graph)
+        y = torch.from_numpy(wl.y).to(dev)
+        sig = torch.from_numpy(wl.sigma).to(dev)
+        syn = torch.from_numpy(wl.s).to(dev)
+        x = torch.from_numpy(wl.x).to(dev)
+        for sched in ("flooding", "layered"):
+            dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, schedule=sched)
+            holder = {}
+
+            def step():
+                holder["o"] = dec.decode_y(y, sig, syn, cap, early_term=True)
+            for _ in range(2):
+                step()
+            ms = time_steps(step, steps, 0, stream, barrier) / steps
+            o = holder["o"]
+            frame_err = (o["bits"] != x).any(dim=1) | (o["converged"] == 0)
+            res[f"beta{beta}_{sched}"] = {
+                "ms_per_decode": ms, "value": a.batch * a.n / (ms * 1e-3) / 1e6, "unit": UNIT,
+                "mean_iters": float(o["iters_used"].float().mean()),
+                "max_iters": int(o["iters_used"].max()),
+                "fer": float(frame_err.float().mean()), "frames": a.batch}
+            dec.close()
+    g.close()
+    return res
 
 
 def main():
@@ -623,6 +667,9 @@ def main():
         vo = "accumulate" if a.vn_update == "gather" else "gather"
         for m in (a.msg, other):
             sub[f"rate{a.rate}_{m}_{vo}"] = sub_record(a.rate, m, a, rank, dev, dist, barrier, peak, vo)
+        sub[f"rate{a.rate}_{a.msg}_layered"] = sub_record(a.rate, a.msg, a, rank, dev, dist, barrier, peak,
+                                                          "gather", "layered")
+        sub["schedules_converging"] = schedule_comparison(a, dev, barrier)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

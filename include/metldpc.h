@@ -107,6 +107,28 @@ typedef struct {
 } mld_graph_stats;
 int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out);
 
+/* ---- layers for the layered (serial) schedule -----------------------------
+ * The layered schedule updates the checks one after another, each from the
+ * latest messages of the others (the check and variable updates of Methods,
+ * Steps 3-4, taken check by check instead of all at once; the paper runs the
+ * flooding schedule).  Checks that share no VN of degree >= 2 give the same
+ * result in either order, so the serial order is given as layers of such
+ * checks: layer 0's checks first (in any order among themselves), then
+ * layer 1's, and so on.
+ * mld_graph_set_layers: layer_of_check = host int32 [n_cn], in the caller's
+ *   check numbering, values in [0, n_layers); or NULL to build the default:
+ *   the checks of each shape (edges to VNs of degree >= 2, degree-1 VNs) split
+ *   by first fit, in check order, into layers whose checks share no such VN,
+ *   layers numbered shape after shape.  Replaces any earlier layering; must
+ *   not run while a decode on the graph is in flight.  Errors: MLD_EINVAL
+ *   (null graph, layer out of range, a check with more than 8 edges or more
+ *   than one degree-1 VN), MLD_EGRAPH (two checks of one layer share a VN of
+ *   degree >= 2), MLD_ENOMEM, MLD_ECUDA.
+ * mld_graph_layers_get: the current layering (layer_of_check may be NULL to
+ *   read only *n_layers); MLD_EINVAL if the graph has none. */
+int mld_graph_set_layers(mld_graph *g, const int32_t *layer_of_check, int32_t n_layers);
+int mld_graph_layers_get(const mld_graph *g, int32_t *layer_of_check, int32_t *n_layers);
+
 /* ---- synthetic code ensemble ----------------------------------------------
  * The seeded multi-edge-type ensemble the decoder is benchmarked on, built on
  * the host.  (The paper decodes PEG-built MET codes whose degree
@@ -162,16 +184,31 @@ int mld_graph_generate(double rate, int32_t n, int32_t d2, uint64_t seed, mld_gr
  *                  width and a graph whose checks all have at most 8 edges and
  *                  at most one degree-1 VN (MLD_EINVAL otherwise), and takes
  *                  two more posterior arrays of device memory.
+ *   schedule   : MLD_SCHED_FLOODING (0, default): every check, then every
+ *                  VN, per iteration (Methods, Steps 3-4);
+ *                MLD_SCHED_LAYERED (1): the checks are updated one layer at a
+ *                  time (see mld_graph_set_layers), each from the messages
+ *                  its predecessors in the same iteration have just sent,
+ *                  and the posteriors follow every layer (no separate
+ *                  variable update).  One iteration updates every check
+ *                  once.  Needs the default slab width, MLD_VN_GATHER and a
+ *                  graph whose checks all have at most 8 edges and at most
+ *                  one degree-1 VN (MLD_EINVAL otherwise); if the graph has
+ *                  no layering yet, the default one is built here.  Plans
+ *                  (mld_plan_create) and mld_decode_noalloc run flooding.
  * Errors: MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA. */
-#define MLD_VN_GATHER     0
-#define MLD_VN_ACCUMULATE 1
+#define MLD_VN_GATHER      0
+#define MLD_VN_ACCUMULATE  1
+#define MLD_SCHED_FLOODING 0
+#define MLD_SCHED_LAYERED  1
 typedef struct {
     int32_t msg_dtype;
     int32_t max_batch;
     float lmax;
     int32_t slab_width;
     int32_t vn_update;
-    int32_t reserved[11];  /* must be zero */
+    int32_t schedule;
+    int32_t reserved[10];  /* must be zero */
 } mld_opts;
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out);
 int mld_decoder_destroy(mld_decoder *d);

@@ -25,6 +25,7 @@ MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA, MLD_ETIMEOUT, MLD_EGRAPH = -1, -2, -3, -4, -5
 MLD_MSG_F32, MLD_MSG_F16 = 0, 1
 MLD_EARLY_TERM, MLD_DEVICE_PTRS = 0x1, 0x2
 MLD_VN_GATHER, MLD_VN_ACCUMULATE = 0, 1
+MLD_SCHED_FLOODING, MLD_SCHED_LAYERED = 0, 1
 
 _STATUS = {MLD_EINVAL: "MLD_EINVAL", MLD_ENOMEM: "MLD_ENOMEM", MLD_ECUDA: "MLD_ECUDA",
            MLD_ETIMEOUT: "MLD_ETIMEOUT", MLD_EGRAPH: "MLD_EGRAPH"}
@@ -36,7 +37,7 @@ EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destr
            "mld_decoder_timing_read", "mld_decode_noalloc", "mld_plan_create", "mld_plan_launch",
            "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_wbp_forward", "mld_wbp_backward",
            "mld_tape_destroy", "mld_phi_eval", "mld_ensemble_size", "mld_ensemble_edges",
-           "mld_graph_generate")
+           "mld_graph_generate", "mld_graph_set_layers", "mld_graph_layers_get")
 
 
 class MldError(RuntimeError):
@@ -54,7 +55,8 @@ class GraphStats(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("msg_dtype", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("lmax", ctypes.c_float), ("slab_width", ctypes.c_int32),
-                ("vn_update", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("vn_update", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
 
 
 class Timing(ctypes.Structure):
@@ -90,6 +92,8 @@ def _load() -> ctypes.CDLL:
                                               P, P, P, I64]),
         "mld_graph_generate": (ctypes.c_int, [ctypes.c_double, I32, I32, ctypes.c_uint64, ctypes.POINTER(P)]),
         "mld_graph_stats_get": (ctypes.c_int, [P, ctypes.POINTER(GraphStats)]),
+        "mld_graph_set_layers": (ctypes.c_int, [P, P, I32]),
+        "mld_graph_layers_get": (ctypes.c_int, [P, P, ctypes.POINTER(I32)]),
         "mld_decoder_create": (ctypes.c_int, [P, ctypes.POINTER(Opts), ctypes.POINTER(P)]),
         "mld_decoder_destroy": (ctypes.c_int, [P]),
         "mld_decode": (ctypes.c_int, [P, P, P, I32, I32, U32, P, P, P, P, P]),
@@ -222,6 +226,24 @@ class Graph:
         """From any object with n_vn, n_cn, edge_vn, edge_cn (and edge_type)."""
         return cls(g.edge_vn, g.edge_cn, g.n_vn, g.n_cn, getattr(g, "edge_type", None))
 
+    def set_layers(self, layer_of_check=None):
+        """Layering of the checks for the layered schedule (mld_graph_set_layers);
+        None builds the library's default first fit."""
+        if layer_of_check is None:
+            _check(lib().mld_graph_set_layers(self._h, None, 0))
+            return
+        lay = np.ascontiguousarray(layer_of_check, dtype=np.int32)
+        if lay.shape != (self.n_cn,):
+            raise ValueError("layer_of_check must be [n_cn]")
+        _check(lib().mld_graph_set_layers(self._h, _ptr(lay), int(lay.max(initial=-1)) + 1))
+
+    def layers(self):
+        """(layer_of_check int32 [n_cn], n_layers) of the current layering."""
+        n = ctypes.c_int32()
+        out = np.empty(self.n_cn, dtype=np.int32)
+        _check(lib().mld_graph_layers_get(self._h, _ptr(out), ctypes.byref(n)))
+        return out, int(n.value)
+
     @property
     def handle(self):
         return self._h
@@ -243,16 +265,20 @@ class Decoder:
 
     ``vn_update``: "gather" (default; deterministic variable update) or
     "accumulate" (the check update adds its messages to the next
-    posteriors; fixed-iteration calls only, see mld_opts)."""
+    posteriors; fixed-iteration calls only, see mld_opts).
+    ``schedule``: "flooding" (default) or "layered" (checks one layer at a
+    time, see Graph.set_layers)."""
 
     def __init__(self, graph: Graph, max_batch: int, msg_dtype: str = "f32",
-                 lmax: float = 25.0, slab_width: int = 0, vn_update: str = "gather"):
+                 lmax: float = 25.0, slab_width: int = 0, vn_update: str = "gather",
+                 schedule: str = "flooding"):
         o = Opts()
         o.msg_dtype = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
         o.max_batch = int(max_batch)
         o.lmax = float(lmax)
         o.slab_width = int(slab_width)
         o.vn_update = {"gather": MLD_VN_GATHER, "accumulate": MLD_VN_ACCUMULATE}[vn_update]
+        o.schedule = {"flooding": MLD_SCHED_FLOODING, "layered": MLD_SCHED_LAYERED}[schedule]
         h = ctypes.c_void_p()
         _check(lib().mld_decoder_create(graph.handle, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

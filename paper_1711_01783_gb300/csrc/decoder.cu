@@ -200,6 +200,39 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         int s = syndrome_round(0, false);
         if (s != MLD_OK) return s;
     }
+    if (d->schedule == MLD_SCHED_LAYERED) {
+        // layered schedule: layer after layer, each launch updates messages
+        // and posteriors in place; decisions after the last iteration (every
+        // iteration under early termination)
+        const int64_t n_launch = static_cast<int64_t>(g->layer_launches.size());
+        for (int32_t l = 1; l <= iters; ++l) {
+            const bool last = (l == iters);
+            ca.final_pass = (last || et) ? 1 : 0;
+            ca.hb1 = hb1_of(l);
+            d->sample_now = ((l - 1) % d->timing_every) == 0;
+            int s = timed_launch(d, kClsCheck, st, "k_check_layered", [&] {
+                for (const mld::LayerLaunch &ll : g->layer_launches) {
+                    const mld::CheckClass &k = h.classes[ll.cls];
+                    ClassLaunch cl{k.c0, ll.count, k.dc, k.dc + k.dd, k.e0, k.s0,
+                                   grid_x(static_cast<int64_t>(ll.count) * TPC)};
+                    launch_layered<MsgT, W>(ca, cl, g->lpos + ll.off, slabs, st);
+                }
+            }, static_cast<int>(n_launch));
+            if (s != MLD_OK) return s;
+            if (last || et) {
+                if (h.n_core > 0) {
+                    s = timed_launch(d, kClsVar, st, "k_hard_bits", [&] {
+                        k_hard_bits<W><<<dim3(grid_x(static_cast<int64_t>(h.n_core) * (W / 8)), slabs), kBlock, 0,
+                                         st>>>(d->Lv, h.n_core, d->hb_core);
+                    });
+                    if (s != MLD_OK) return s;
+                }
+                s = syndrome_round(l, et);
+                if (s != MLD_OK) return s;
+            }
+        }
+        iters = 0;  // the flooding loop below does nothing
+    }
     for (int32_t l = 1; l <= iters; ++l) {
         const bool last = (l == iters);
         ca.final_pass = (last || et) ? 1 : 0;
@@ -427,7 +460,7 @@ int mld_graph_create(const int32_t *edge_vn, const int32_t *edge_cn, const uint8
 int mld_graph_destroy(mld_graph *g) {
     if (!g) return MLD_OK;
     dfree(g->cptr); dfree(g->col); dfree(g->dptr); dfree(g->vptr); dfree(g->vedge);
-    dfree(g->unit); dfree(g->cint); dfree(g->etype_core); dfree(g->etype_deg1);
+    dfree(g->unit); dfree(g->cint); dfree(g->etype_core); dfree(g->etype_deg1); dfree(g->lpos);
     delete g;
     return MLD_OK;
 }
@@ -447,13 +480,45 @@ int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out) {
     return MLD_OK;
 }
 
+int mld_graph_set_layers(mld_graph *g, const int32_t *layer_of_check, int32_t n_layers) {
+    mld::clear_error();
+    if (!g) return mld::fail(MLD_EINVAL, "graph_set_layers: null graph");
+    std::vector<mld::LayerLaunch> launches;
+    std::vector<int32_t> pos, user;
+    int32_t nl = 0;
+    int s = mld::build_layers(g->h, layer_of_check, n_layers, &launches, &pos, &user, &nl);
+    if (s != MLD_OK) return s;
+    s = check_device(g->device);
+    if (s != MLD_OK) return s;
+    int32_t *dpos = nullptr;
+    s = upload(&dpos, pos);
+    if (s != MLD_OK) return s;
+    dfree(g->lpos);
+    g->lpos = dpos;
+    g->layer_launches = std::move(launches);
+    g->layer_user = std::move(user);
+    g->n_layers = nl;
+    return MLD_OK;
+}
+
+int mld_graph_layers_get(const mld_graph *g, int32_t *layer_of_check, int32_t *n_layers) {
+    mld::clear_error();
+    if (!g || !n_layers) return mld::fail(MLD_EINVAL, "graph_layers_get: null pointer");
+    if (!g->lpos) return mld::fail(MLD_EINVAL, "graph_layers_get: the graph has no layering");
+    *n_layers = g->n_layers;
+    if (layer_of_check) std::copy(g->layer_user.begin(), g->layer_user.end(), layer_of_check);
+    return MLD_OK;
+}
+
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out) {
     mld::clear_error();
     if (!g || !opts || !out) return mld::fail(MLD_EINVAL, "decoder_create: null pointer");
-    for (int i = 0; i < 11; ++i)
+    for (int i = 0; i < 10; ++i)
         if (opts->reserved[i] != 0) return mld::fail(MLD_EINVAL, "decoder_create: reserved field not zero");
     if (opts->vn_update != MLD_VN_GATHER && opts->vn_update != MLD_VN_ACCUMULATE)
         return mld::fail(MLD_EINVAL, "decoder_create: unknown vn_update");
+    if (opts->schedule != MLD_SCHED_FLOODING && opts->schedule != MLD_SCHED_LAYERED)
+        return mld::fail(MLD_EINVAL, "decoder_create: unknown schedule");
     if (opts->msg_dtype != MLD_MSG_F32 && opts->msg_dtype != MLD_MSG_F16)
         return mld::fail(MLD_EINVAL, "decoder_create: unknown msg_dtype");
     if (opts->max_batch < 1) return mld::fail(MLD_EINVAL, "decoder_create: max_batch < 1");
@@ -469,8 +534,20 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
             return mld::fail(MLD_EINVAL, "decoder_create: posterior accumulation needs every check to have at "
                                          "most 8 edges and at most one degree-1 VN");
     }
+    if (opts->schedule == MLD_SCHED_LAYERED) {
+        if (W != ((opts->msg_dtype == MLD_MSG_F16) ? 64 : 32))
+            return mld::fail(MLD_EINVAL, "decoder_create: the layered schedule needs the default slab width");
+        if (opts->vn_update != MLD_VN_GATHER)
+            return mld::fail(MLD_EINVAL, "decoder_create: the layered schedule updates posteriors in place "
+                                         "(vn_update must be MLD_VN_GATHER)");
+    }
     int s = check_device(g->device);
     if (s != MLD_OK) return s;
+    if (opts->schedule == MLD_SCHED_LAYERED && !g->lpos) {
+        // no layering given: the default first fit per check class
+        s = mld_graph_set_layers(const_cast<mld_graph *>(g), nullptr, 0);
+        if (s != MLD_OK) return s;
+    }
     mld_decoder *d = new (std::nothrow) mld_decoder();
     if (!d) return mld::fail(MLD_ENOMEM, "decoder_create: host allocation");
     d->g = g;
@@ -478,6 +555,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     d->msg = opts->msg_dtype;
     d->W = W;
     d->vn_update = opts->vn_update;
+    d->schedule = opts->schedule;
     d->max_batch = opts->max_batch;
     d->max_slabs = (opts->max_batch + W - 1) / W;
     set_units(d, opts->lmax > 0.f ? opts->lmax : 25.f);

@@ -142,4 +142,91 @@ int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
     return MLD_OK;
 }
 
+int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_layers,
+                 std::vector<LayerLaunch> *launches, std::vector<int32_t> *pos,
+                 std::vector<int32_t> *layer_user, int32_t *n_layers_out) {
+    const int32_t m = h.n_cn;
+    for (const CheckClass &cl : h.classes)
+        if (!(cl.dc == 0 && cl.dd == 0) && (cl.dc < 0 || cl.dd > 1 || cl.dc + cl.dd > kMaxRegDeg))
+            return fail(MLD_EINVAL, "layers: the layered schedule needs every check to have at most " +
+                                        std::to_string(kMaxRegDeg) + " edges and at most one degree-1 VN");
+    // class of every internal check
+    std::vector<int32_t> cls_of(m, 0);
+    for (size_t k = 0; k < h.classes.size(); ++k)
+        for (int32_t i = 0; i < h.classes[k].count; ++i) cls_of[h.classes[k].c0 + i] = static_cast<int32_t>(k);
+    std::vector<int32_t> lay(m, 0);  // layer of internal check
+    int32_t nl = 0;
+    if (layer_of_check) {
+        if (n_layers < 1 && m > 0) return fail(MLD_EINVAL, "layers: n_layers < 1");
+        for (int32_t ci = 0; ci < m; ++ci) {
+            const int32_t L = layer_of_check[h.cuser[ci]];
+            if (L < 0 || L >= n_layers)
+                return fail(MLD_EINVAL, "layers: layer of check " + std::to_string(h.cuser[ci]) + " out of range");
+            lay[ci] = L;
+        }
+        nl = n_layers;
+    } else {
+        // first fit per class, in the class's check order; layers numbered
+        // class after class
+        const int32_t maxc = std::max<int32_t>(1, h.max_vn_deg) * kMaxRegDeg + 1;  // bound on first-fit layers
+        const int32_t words = (maxc + 63) / 64;
+        std::vector<uint64_t> used;
+        for (const CheckClass &cl : h.classes) {
+            if (cl.dc == 0 && cl.dd == 0) {
+                for (int32_t i = 0; i < cl.count; ++i) lay[cl.c0 + i] = nl;
+                continue;
+            }
+            used.assign(static_cast<size_t>(h.n_core) * words, 0ull);
+            int32_t top = 0;
+            for (int32_t i = 0; i < cl.count; ++i) {
+                const int32_t ci = cl.c0 + i;
+                int32_t L = 0;
+                for (;; ++L) {
+                    bool free = true;
+                    for (int32_t e = h.cptr[ci]; e < h.cptr[ci + 1] && free; ++e)
+                        if ((used[static_cast<size_t>(h.col[e]) * words + L / 64] >> (L % 64)) & 1ull) free = false;
+                    if (free) break;
+                }
+                for (int32_t e = h.cptr[ci]; e < h.cptr[ci + 1]; ++e)
+                    used[static_cast<size_t>(h.col[e]) * words + L / 64] |= 1ull << (L % 64);
+                lay[ci] = nl + L;
+                top = std::max(top, L + 1);
+            }
+            nl += top;
+        }
+    }
+    // internal checks ordered by (layer, class, position)
+    std::vector<int32_t> ord(m);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+        if (lay[a] != lay[b]) return lay[a] < lay[b];
+        return cls_of[a] < cls_of[b];
+    });
+    // no core VN twice in a layer
+    std::vector<int32_t> stamp(h.n_core, -1);
+    for (int32_t ci : ord)
+        for (int32_t e = h.cptr[ci]; e < h.cptr[ci + 1]; ++e) {
+            if (stamp[h.col[e]] == lay[ci])
+                return fail(MLD_EGRAPH, "layers: two checks of layer " + std::to_string(lay[ci]) +
+                                            " share a VN of degree >= 2 (check " + std::to_string(h.cuser[ci]) + ")");
+            stamp[h.col[e]] = lay[ci];
+        }
+    launches->clear();
+    pos->clear();
+    pos->reserve(m);
+    for (int32_t i = 0; i < m; ++i) {
+        const int32_t ci = ord[i];
+        const CheckClass &cl = h.classes[cls_of[ci]];
+        if (cl.dc == 0 && cl.dd == 0) continue;  // nothing to send
+        if (launches->empty() || launches->back().layer != lay[ci] || launches->back().cls != cls_of[ci])
+            launches->push_back(LayerLaunch{lay[ci], cls_of[ci], static_cast<int32_t>(pos->size()), 0});
+        pos->push_back(ci - cl.c0);
+        launches->back().count++;
+    }
+    layer_user->assign(m, 0);
+    for (int32_t ci = 0; ci < m; ++ci) (*layer_user)[h.cuser[ci]] = lay[ci];
+    *n_layers_out = nl;
+    return MLD_OK;
+}
+
 }  // namespace mld

@@ -65,6 +65,21 @@ int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
                      const uint8_t *edge_type, int64_t n_edges, int32_t n_vn,
                      int32_t n_cn, HostGraph *out);
 
+// Layered schedule: the checks of one layer share no core VN.  A layer's
+// checks of one class form one launch; `off` indexes the class positions
+// (j, check c0 + j of the class) of the launch in the graph's layer table.
+struct LayerLaunch {
+    int32_t layer, cls, off, count;
+};
+
+// Validate a layering (layer of every check in the caller's numbering; NULL
+// computes a first fit per class) and build the launch list and the table of
+// class positions, ordered by (layer, class, position).  Every check with
+// edges must be in a register class.
+int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_layers,
+                 std::vector<LayerLaunch> *launches, std::vector<int32_t> *pos,
+                 std::vector<int32_t> *layer_user, int32_t *n_layers_out);
+
 }  // namespace mld
 
 struct mld_graph {
@@ -78,6 +93,13 @@ struct mld_graph {
     std::vector<mld::ClassLaunch> launches[4];
     // every check is in a register class (enables the fused syndrome check)
     bool fusable = false;
-    // every check with edges is in a register class (posterior accumulation)
+    // every check with edges is in a register class (posterior accumulation,
+    // layered schedule)
     bool acc_ok = false;
+    // layered schedule: launches in order, class positions (device), and the
+    // layer of every check in the caller's numbering
+    std::vector<mld::LayerLaunch> layer_launches;
+    std::vector<int32_t> layer_user;
+    int32_t n_layers = 0;
+    int32_t *lpos = nullptr;
 };

@@ -659,6 +659,159 @@ void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cuda
 }
 
 // ---------------------------------------------------------------------------
+// Layered schedule: the checks are updated one layer at a time, every check
+// from the latest messages.  The checks of a layer share no core VN, so a
+// check owns the posteriors of its core VNs while its layer runs: it forms
+// q = L_v - r_old (Eq. 4 with the current messages), the new r (Eqs. 2-3,
+// as in check_regular) and L_v <- (L_v - r_old) + r_new in place.
+// ---------------------------------------------------------------------------
+template <typename MsgT, int W, int DC, int DD>
+__device__ __forceinline__ void check_layered(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
+                                              int slab, bool valid) {
+    constexpr int D = DC + DD;
+    constexpr int F = DecodeFit<MsgT>::value;
+    constexpr int NB = W / 8;
+    const int32_t c = cl.c0 + j;
+    const int32_t e0 = cl.e0 + j * DC;
+    const int32_t s0 = cl.s0 + j * DD;
+    const float lmax = a.lmax, amin = a.amin;
+    const uint32_t sb =
+        (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >>
+         (lane0 & 7));
+    const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
+    MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
+    // the posteriors are written by this kernel: plain (coherent) loads
+    float *lvb = const_cast<float *>(a.Lv) + static_cast<size_t>(slab) * a.n_core * W + lane0;
+    const float *p1b = a.phi1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
+
+    float f[D][kK];
+    uint32_t par[kK];
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) par[kk] = ((sb >> kk) & 1u) << 31;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        if (i < DC) {
+            const int32_t v = __ldg(a.col + e0 + i);
+            const float4 lv = *reinterpret_cast<const float4 *>(lvb + static_cast<size_t>(v) * W);
+            const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
+            const float4 q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
+            const float4 m = make_float4(fabsf(q.x), fabsf(q.y), fabsf(q.z), fabsf(q.w));
+            const float4 ph = phi4_floor<F>(m, amin);
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) {
+                const uint32_t qb = fbits(f4get(q, kk));
+                f[i][kk] = bitsf(fbits(f4get(ph, kk)) | (qb & kSign));
+                par[kk] ^= qb;
+            }
+        } else {
+            const float4 p = ldf4(p1b + static_cast<size_t>(s0 + i - DC) * W);
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) {
+                f[i][kk] = f4get(p, kk);
+                par[kk] ^= fbits(f[i][kk]);
+            }
+        }
+    }
+    float pre[D][kK];
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) {
+        if (D >= 2) pre[1][kk] = fabsf(f[0][kk]);
+#pragma unroll
+        for (int i = 2; i < D; ++i) pre[i][kk] = pre[i - 1][kk] + fabsf(f[i - 1][kk]);
+    }
+    float suf[kK];
+#pragma unroll
+    for (int i = D - 1; i >= 0; --i) {
+        if (i < DC || a.final_pass) {
+            float4 o;
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) {
+                float v;
+                if (D == 1) v = amin;
+                else if (i == D - 1) v = pre[i][kk];
+                else if (i == 0) v = suf[kk];
+                else v = pre[i][kk] + suf[kk];
+                f4set(o, kk, v);
+            }
+            float4 mm = phi4_floor<F>(o, amin);
+            if (D <= 2) mm = make_float4(fminf(mm.x, lmax), fminf(mm.y, lmax), fminf(mm.z, lmax), fminf(mm.w, lmax));
+            float4 rv;
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk)
+                f4set(rv, kk, bitsf(fbits(f4get(mm, kk)) | ((par[kk] ^ fbits(f[i][kk])) & kSign)));
+            if (i < DC) {
+                if (valid) {
+                    MsgT *rp = rb + static_cast<size_t>(e0 + i) * W;
+                    const float4 ro = Msg<MsgT>::load(rp);
+                    if (donenib) {  // converged lanes keep their messages
+                        if (donenib & 1) rv.x = ro.x;
+                        if (donenib & 2) rv.y = ro.y;
+                        if (donenib & 4) rv.z = ro.z;
+                        if (donenib & 8) rv.w = ro.w;
+                    }
+                    const float4 st = Msg<MsgT>::store_get(rp, rv);
+                    float *lp = lvb + static_cast<size_t>(__ldg(a.col + e0 + i)) * W;
+                    const float4 lv = *reinterpret_cast<const float4 *>(lp);
+                    float4 ln = make_float4((lv.x - ro.x) + st.x, (lv.y - ro.y) + st.y, (lv.z - ro.z) + st.z,
+                                            (lv.w - ro.w) + st.w);
+                    if (donenib) {  // and their posteriors
+                        if (donenib & 1) ln.x = lv.x;
+                        if (donenib & 2) ln.y = lv.y;
+                        if (donenib & 4) ln.z = lv.z;
+                        if (donenib & 8) ln.w = lv.w;
+                    }
+                    *reinterpret_cast<float4 *>(lp) = ln;
+                }
+            } else {
+                emit_deg1<MsgT, W>(a, slab, s0 + i - DC, lane0, rv, donenib, valid);
+            }
+        }
+        if (i > 0) {
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) suf[kk] = (i == D - 1) ? fabsf(f[i][kk]) : suf[kk] + fabsf(f[i][kk]);
+        }
+    }
+}
+
+// One layer's checks of one class: pos[k] is the class position of the
+// launch's k-th check.  A thread past the end works on the last check and
+// stores nothing (its shuffle pair stays whole).
+template <typename MsgT, int W, int DC, int DD>
+__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_layered(CnArgs a, ClassLaunch cl,
+                                                                                  const int32_t *pos) {
+    constexpr int TPC = W / kK;
+    const int slab = blockIdx.y;
+    if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    int32_t k = static_cast<int32_t>(t / TPC);
+    const bool valid = k < cl.count;
+    if (!valid) k = cl.count - 1;
+    check_layered<MsgT, W, DC, DD>(a, cl, __ldg(pos + k), static_cast<int>(t % TPC) * kK, slab, valid);
+}
+
+// The layered schedule is built for the default slab width of each message
+// type, and for the register classes (at most one degree-1 VN per check).
+template <typename MsgT, int W>
+void launch_layered(const CnArgs &ca, const ClassLaunch &cl, const int32_t *pos, int slabs, cudaStream_t st) {
+    if constexpr (kAccWidth<MsgT, W>) {
+        const dim3 grid(cl.blocks, slabs);
+        const int dd = cl.deg - cl.dc;
+#define MLD_LCASE(DCV, DDV)                                                        \
+    case (DCV) * 2 + (DDV):                                                        \
+        k_check_layered<MsgT, W, DCV, DDV><<<grid, kBlock, 0, st>>>(ca, cl, pos); \
+        return;
+        switch (cl.dc * 2 + dd) {
+            MLD_LCASE(1, 0) MLD_LCASE(2, 0) MLD_LCASE(3, 0) MLD_LCASE(4, 0)
+            MLD_LCASE(5, 0) MLD_LCASE(6, 0) MLD_LCASE(7, 0) MLD_LCASE(8, 0)
+            MLD_LCASE(0, 1) MLD_LCASE(1, 1) MLD_LCASE(2, 1) MLD_LCASE(3, 1)
+            MLD_LCASE(4, 1) MLD_LCASE(5, 1) MLD_LCASE(6, 1) MLD_LCASE(7, 1)
+            default: break;
+        }
+#undef MLD_LCASE
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Variable update (Eqs. 4-5) for core VNs: L_v = L_ch + sum of incoming r.
 // ---------------------------------------------------------------------------
 struct VnArgs {
@@ -1104,6 +1257,7 @@ struct mld_decoder {
     int32_t *status = nullptr;
     // posterior accumulation (MLD_VN_ACCUMULATE): two more posterior buffers
     int vn_update = MLD_VN_GATHER;
+    int schedule = MLD_SCHED_FLOODING;
     float *Lv2 = nullptr, *Lv3 = nullptr;
     // staging buffers for host pointers
     float *in_stage = nullptr, *sigma_stage = nullptr, *post_stage = nullptr;

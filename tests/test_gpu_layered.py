@@ -1,0 +1,156 @@
+"""The layered (serial-schedule) decoder against the FP64 layered oracle.
+
+Both sides take the same layering (synthetic.check_layers), so the GPU's
+layer-by-layer updates and the oracle's check-by-check order are the same
+schedule.  Criteria: one iteration from identical inputs stays within the
+per-iteration error bounds of the flooding decoder (tests/test_gpu_parity.py)
+with a factor 2 for the errors that later layers of the same iteration
+inherit through the posteriors; after N iterations the flooding criteria
+(>= 99.99 % of bits, identical converged flags and iteration counts with
+float messages in stable regimes; per-frame criteria otherwise); cycle-free
+codes reach bitwise MAP; converged words satisfy H x = s.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import check_layers, layer_order, make_workload, preset_graph
+from tests import brute
+from tests.parity import _check_frames, _cp_interval, _llr32, _np, _syndrome_holds
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mld():
+    import paper_1711_01783_gb300 as m
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _layered(mld, g0, B, msg):
+    lay, _ = check_layers(g0)
+    g = mld.Graph.from_edges(g0)
+    g.set_layers(lay)
+    got, n = g.layers()
+    assert np.array_equal(got, lay) and n == lay.max() + 1
+    return g, mld.Decoder(g, B, msg_dtype=msg, schedule="layered"), layer_order(lay)
+
+
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_one_iteration_against_the_layered_oracle(mld, msg):
+    w = make_workload(0.1, 4096, 8, 1, 6000)
+    g, dec, od = _layered(mld, w.graph, 8, msg)
+    L = _llr32(w)
+    out = dec.decode(_dev(L), _dev(w.s), iters=1, want_post=True)
+    ref = oracle.decode_layered(w.graph, L, w.s, iters=1, order=od)
+    d = np.abs(_np(out["post"]).astype(np.float64) - ref["post"])
+    if msg == "f32":
+        bound = 2 * (1e-4 + 1e-5 * np.abs(ref["post"]))
+    else:
+        dv = w.graph.vn_degree()[None, :]
+        bound = 2 * (dv * ((2.0 ** -11 + 2.3e-4) * 25.0 + 2.3e-4) + 1e-4)
+    assert np.all(d <= bound), (d.max(), (d - bound).max())
+    print(f"{msg}: layered one-iteration |dL| max {d.max():.3g} mean {d.mean():.3g}")
+
+
+@pytest.mark.parametrize("msg,beta,iters,et", [
+    ("f32", 0.9, 30, False),
+    ("f32", 0.3, 40, True),
+    ("f16", 0.9, 30, False),
+    ("f16", 0.3, 40, True),
+])
+def test_decode_matches_layered_oracle(mld, msg, beta, iters, et):
+    w = make_workload(0.1, 4096, 8, 1, 6100, beta=beta)
+    g, dec, od = _layered(mld, w.graph, 8, msg)
+    out = dec.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=iters, early_term=et, want_post=True)
+    ref = oracle.decode_layered(w.graph, oracle.channel_llr(w.y, w.sigma), w.s, iters=iters, order=od,
+                                early_term=et)
+    _check_frames(out, ref, w.graph, w.s, msg)
+    if beta == 0.9:
+        assert (_np(out["bits"]) == ref["bits"]).mean() >= 0.9999
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tree_codes_reach_map(mld, seed):
+    rng = np.random.default_rng(700 + seed)
+    t = brute.random_tree_code(rng, int(rng.integers(6, 15)))
+    H = brute.parity_matrix(t)
+    B = 8
+    x = rng.integers(0, 2, (B, t.n_vn)).astype(np.uint8)
+    s = ((x.astype(np.int64) @ H.T) % 2).astype(np.uint8)
+    L = ((1 - 2.0 * x) * 0.8 + rng.normal(0, 1.2, x.shape)).astype(np.float32)
+    g = mld.Graph(t.edge_vn, t.edge_cn, t.n_vn, t.n_cn)   # default layering
+    dec = mld.Decoder(g, B, schedule="layered")
+    out = dec.decode(_dev(L), _dev(s), iters=t.n_vn + 2, want_post=True)
+    for b in range(B):
+        np.testing.assert_allclose(_np(out["post"])[b], brute.map_llr(H, s[b], L[b]), rtol=1e-4, atol=1e-4)
+
+
+def test_frame_error_rate_and_fewer_iterations_than_flooding(mld):
+    """Near the ensemble's threshold (n = 4096, beta = 0.42): the layered
+    decoder's FER lies in the layered oracle's 95 % interval, and frames
+    converge in fewer iterations than with flooding."""
+    B = 128
+    g0 = preset_graph(0.1, 4096, 1)
+    w = make_workload(0.1, 4096, B, 1, 6200, beta=0.42, graph=g0)
+    g, dec, od = _layered(mld, g0, B, "f32")
+    ref = oracle.decode_layered(g0, oracle.channel_llr(w.y, w.sigma), w.s, iters=60, order=od, early_term=True)
+    out = dec.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=60, early_term=True)
+    _check_frames(out, ref, g0, w.s, "f32", near_threshold=True)
+    flo = mld.Decoder(g, B, msg_dtype="f32").decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=60,
+                                                      early_term=True)
+    both = _np(out["converged"]).astype(bool) & _np(flo["converged"]).astype(bool)
+    it_l, it_f = _np(out["iters_used"])[both].mean(), _np(flo["iters_used"])[both].mean()
+    k = int(B - ref["converged"].sum())
+    lo, hi = _cp_interval(k, B)
+    print(f"layered FER {1 - _np(out['converged']).mean():.3f} (oracle {k / B:.3f} [{lo:.3f}, {hi:.3f}]), "
+          f"flooding FER {1 - _np(flo['converged']).mean():.3f}; mean iterations on frames both decode: "
+          f"layered {it_l:.2f}, flooding {it_f:.2f}")
+    assert it_l < 0.75 * it_f
+
+
+def test_full_size_converging_regime(mld):
+    """n = 10^6, 64 codewords, beta = 0.40, early termination (the launch the
+    benchmark's schedule comparison times); the oracle decodes three frames."""
+    w = make_workload(0.1, 1_000_000, 64, 2, 7000, beta=0.40)
+    lay, _ = check_layers(w.graph)
+    od = layer_order(lay)
+    sample = [0, 37, 63]
+    ref = oracle.decode_layered(w.graph, oracle.channel_llr(w.y[sample], w.sigma[sample]), w.s[sample], iters=100,
+                                order=od, early_term=True)
+    g = mld.Graph.from_edges(w.graph)
+    g.set_layers(lay)
+    for msg in ("f32", "f16"):
+        dec = mld.Decoder(g, 64, msg_dtype=msg, schedule="layered")
+        out = dec.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), iters=100, early_term=True, want_post=True)
+        conv = _np(out["converged"]).astype(bool)
+        assert np.array_equal(_syndrome_holds(w.graph, _np(out["bits"]), w.s), conv)
+        sub = {k: (v[sample] if v is not None else None) for k, v in out.items()}
+        _check_frames(sub, ref, w.graph, w.s[sample], msg)
+        print(f"{msg}: layered at n=1e6 converged {conv.sum()}/64, mean iterations "
+              f"{_np(out['iters_used']).mean():.2f} (oracle sample {ref['iters_used'].tolist()})")
+
+
+def test_invalid_layerings_are_refused(mld):
+    g0 = preset_graph(0.1, 4096, 1)
+    g = mld.Graph.from_edges(g0)
+    with pytest.raises(mld.MldError) as e:
+        g.set_layers(np.zeros(g.n_cn, np.int32))        # every check in one layer: shared VNs
+    assert e.value.status == mld.MLD_EGRAPH
+    with pytest.raises(ValueError):
+        g.set_layers(np.zeros(3, np.int32))
+    with pytest.raises(mld.MldError):
+        mld.Decoder(g, 8, msg_dtype="f16", slab_width=16, schedule="layered")
+    with pytest.raises(mld.MldError):
+        mld.Decoder(g, 8, msg_dtype="f32", vn_update="accumulate", schedule="layered")
+    # plans run the flooding schedule
+    w = make_workload(0.1, 4096, 2, 1, 6300, graph=g0)
+    dec = mld.Decoder(g, 2, schedule="layered")
+    with pytest.raises(mld.MldError):
+        mld.Plan([dict(decoder=dec, y=_dev(w.y), sigma=_dev(w.sigma), syndrome=_dev(w.s), max_iters=5)])
