@@ -121,9 +121,8 @@ int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out);
  *   by first fit, in check order, into layers whose checks share no such VN,
  *   layers numbered shape after shape.  Replaces any earlier layering; must
  *   not run while a decode on the graph is in flight.  Errors: MLD_EINVAL
- *   (null graph, layer out of range, a check with more than 8 edges or more
- *   than one degree-1 VN), MLD_EGRAPH (two checks of one layer share a VN of
- *   degree >= 2), MLD_ENOMEM, MLD_ECUDA.
+ *   (null graph, layer out of range), MLD_EGRAPH (two checks of one layer
+ *   share a VN of degree >= 2), MLD_ENOMEM, MLD_ECUDA.
  * mld_graph_layers_get: the current layering (layer_of_check may be NULL to
  *   read only *n_layers); MLD_EINVAL if the graph has none. */
 int mld_graph_set_layers(mld_graph *g, const int32_t *layer_of_check, int32_t n_layers);
@@ -191,11 +190,10 @@ int mld_graph_generate(double rate, int32_t n, int32_t d2, uint64_t seed, mld_gr
  *                  its predecessors in the same iteration have just sent,
  *                  and the posteriors follow every layer (no separate
  *                  variable update).  One iteration updates every check
- *                  once.  Needs the default slab width, MLD_VN_GATHER and a
- *                  graph whose checks all have at most 8 edges and at most
- *                  one degree-1 VN (MLD_EINVAL otherwise); if the graph has
- *                  no layering yet, the default one is built here.  Plans
- *                  (mld_plan_create) and mld_decode_noalloc run flooding.
+ *                  once.  Needs the default slab width and MLD_VN_GATHER
+ *                  (MLD_EINVAL otherwise); if the graph has no layering yet,
+ *                  the default one is built here.  Plans (mld_plan_create)
+ *                  and mld_decode_noalloc run flooding.
  * Errors: MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA. */
 #define MLD_VN_GATHER      0
 #define MLD_VN_ACCUMULATE  1

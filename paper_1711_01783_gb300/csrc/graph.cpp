@@ -146,10 +146,6 @@ int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_la
                  std::vector<LayerLaunch> *launches, std::vector<int32_t> *pos,
                  std::vector<int32_t> *layer_user, int32_t *n_layers_out) {
     const int32_t m = h.n_cn;
-    for (const CheckClass &cl : h.classes)
-        if (!(cl.dc == 0 && cl.dd == 0) && (cl.dc < 0 || cl.dd > 1 || cl.dc + cl.dd > kMaxRegDeg))
-            return fail(MLD_EINVAL, "layers: the layered schedule needs every check to have at most " +
-                                        std::to_string(kMaxRegDeg) + " edges and at most one degree-1 VN");
     // class of every internal check
     std::vector<int32_t> cls_of(m, 0);
     for (size_t k = 0; k < h.classes.size(); ++k)
@@ -168,7 +164,8 @@ int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_la
     } else {
         // first fit per class, in the class's check order; layers numbered
         // class after class
-        const int32_t maxc = std::max<int32_t>(1, h.max_vn_deg) * kMaxRegDeg + 1;  // bound on first-fit layers
+        // first fit needs at most (checks sharing a VN with the check) + 1 layers
+        const int32_t maxc = std::max<int32_t>(1, h.max_vn_deg) * std::max<int32_t>(1, h.max_check_deg) + 1;
         const int32_t words = (maxc + 63) / 64;
         std::vector<uint64_t> used;
         for (const CheckClass &cl : h.classes) {

@@ -789,8 +789,101 @@ __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_layere
     check_layered<MsgT, W, DC, DD>(a, cl, __ldg(pos + k), static_cast<int>(t % TPC) * kK, slab, valid);
 }
 
+// Layered update of a check of any degree (edges read through cptr/dptr);
+// leave-one-out sums as total minus own term, as in check_irregular.  Both
+// threads of a shuffle pair belong to one check.
+template <typename MsgT, int W>
+__device__ __forceinline__ void check_layered_irregular(const CnArgs &a, int32_t c, int lane0, int slab) {
+    constexpr int F = DecodeFit<MsgT>::value;
+    constexpr int NB = W / 8;
+    const int32_t e0 = a.cptr[c], e1 = a.cptr[c + 1];
+    const int32_t s0 = a.dptr[c], s1 = a.dptr[c + 1];
+    const int nce = e1 - e0;
+    const int deg = nce + (s1 - s0);
+    const float lmax = a.lmax, amin = a.amin;
+    const uint32_t sb =
+        (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >>
+         (lane0 & 7));
+    const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
+    MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
+    float *lvb = const_cast<float *>(a.Lv) + static_cast<size_t>(slab) * a.n_core * W + lane0;
+    const float *l1b = a.lch1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
+    auto input = [&](int i) -> float4 {
+        if (i < nce) {
+            const float4 lv = *reinterpret_cast<const float4 *>(lvb + static_cast<size_t>(__ldg(a.col + e0 + i)) * W);
+            const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
+            return make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
+        }
+        return ldf4(l1b + static_cast<size_t>(s0 + i - nce) * W);  // q = L_ch
+    };
+    float S[kK] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t par[kK];
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) par[kk] = ((sb >> kk) & 1u) << 31;
+    for (int i = 0; i < deg; ++i) {
+        const float4 q = input(i);
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) {
+            const float qk = f4get(q, kk);
+            par[kk] ^= fbits(qk);
+            S[kk] += phi_f<F>(clampf(fabsf(qk), amin, lmax));
+        }
+    }
+    // each edge's message and VN are touched only at its own i, so input(i)
+    // still reads the values of pass 1
+    for (int i = 0; i < deg; ++i) {
+        const bool out_core = i < nce;
+        if (!out_core && !a.final_pass) continue;
+        const float4 q = input(i);
+        float4 rv;
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) {
+            const float qk = f4get(q, kk);
+            const float fk = phi_f<F>(clampf(fabsf(qk), amin, lmax));
+            const float mk = fminf(phi_f<F>(clampf(S[kk] - fk, amin, lmax)), lmax);
+            f4set(rv, kk, bitsf(fbits(mk) | ((par[kk] ^ fbits(qk)) & kSign)));
+        }
+        if (out_core) {
+            MsgT *rp = rb + static_cast<size_t>(e0 + i) * W;
+            const float4 ro = Msg<MsgT>::load(rp);
+            if (donenib) {
+                if (donenib & 1) rv.x = ro.x;
+                if (donenib & 2) rv.y = ro.y;
+                if (donenib & 4) rv.z = ro.z;
+                if (donenib & 8) rv.w = ro.w;
+            }
+            const float4 st = Msg<MsgT>::store_get(rp, rv);
+            float *lp = lvb + static_cast<size_t>(__ldg(a.col + e0 + i)) * W;
+            const float4 lv = *reinterpret_cast<const float4 *>(lp);
+            float4 ln = make_float4((lv.x - ro.x) + st.x, (lv.y - ro.y) + st.y, (lv.z - ro.z) + st.z,
+                                    (lv.w - ro.w) + st.w);
+            if (donenib) {
+                if (donenib & 1) ln.x = lv.x;
+                if (donenib & 2) ln.y = lv.y;
+                if (donenib & 4) ln.z = lv.z;
+                if (donenib & 8) ln.w = lv.w;
+            }
+            *reinterpret_cast<float4 *>(lp) = ln;
+        } else {
+            emit_deg1<MsgT, W>(a, slab, s0 + i - nce, lane0, rv, donenib, true);
+        }
+    }
+}
+
+template <typename MsgT, int W>
+__global__ void __launch_bounds__(kBlock) k_check_layered_irregular(CnArgs a, ClassLaunch cl, const int32_t *pos) {
+    constexpr int TPC = W / kK;
+    const int slab = blockIdx.y;
+    if (a.et && slab_all_done<W>(a.done, slab)) return;
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int32_t k = static_cast<int32_t>(t / TPC);
+    if (k >= cl.count) return;  // whole checks, hence whole shuffle pairs
+    check_layered_irregular<MsgT, W>(a, cl.c0 + __ldg(pos + k), static_cast<int>(t % TPC) * kK, slab);
+}
+
 // The layered schedule is built for the default slab width of each message
-// type, and for the register classes (at most one degree-1 VN per check).
+// type.  Classes of at most 8 terms with at most one degree-1 VN run the
+// register kernel of their shape, any other class the runtime-degree kernel.
 template <typename MsgT, int W>
 void launch_layered(const CnArgs &ca, const ClassLaunch &cl, const int32_t *pos, int slabs, cudaStream_t st) {
     if constexpr (kAccWidth<MsgT, W>) {
@@ -800,14 +893,17 @@ void launch_layered(const CnArgs &ca, const ClassLaunch &cl, const int32_t *pos,
     case (DCV) * 2 + (DDV):                                                        \
         k_check_layered<MsgT, W, DCV, DDV><<<grid, kBlock, 0, st>>>(ca, cl, pos); \
         return;
-        switch (cl.dc * 2 + dd) {
-            MLD_LCASE(1, 0) MLD_LCASE(2, 0) MLD_LCASE(3, 0) MLD_LCASE(4, 0)
-            MLD_LCASE(5, 0) MLD_LCASE(6, 0) MLD_LCASE(7, 0) MLD_LCASE(8, 0)
-            MLD_LCASE(0, 1) MLD_LCASE(1, 1) MLD_LCASE(2, 1) MLD_LCASE(3, 1)
-            MLD_LCASE(4, 1) MLD_LCASE(5, 1) MLD_LCASE(6, 1) MLD_LCASE(7, 1)
-            default: break;
+        if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
+            switch (cl.dc * 2 + dd) {
+                MLD_LCASE(1, 0) MLD_LCASE(2, 0) MLD_LCASE(3, 0) MLD_LCASE(4, 0)
+                MLD_LCASE(5, 0) MLD_LCASE(6, 0) MLD_LCASE(7, 0) MLD_LCASE(8, 0)
+                MLD_LCASE(0, 1) MLD_LCASE(1, 1) MLD_LCASE(2, 1) MLD_LCASE(3, 1)
+                MLD_LCASE(4, 1) MLD_LCASE(5, 1) MLD_LCASE(6, 1) MLD_LCASE(7, 1)
+                default: break;
+            }
         }
 #undef MLD_LCASE
+        k_check_layered_irregular<MsgT, W><<<grid, kBlock, 0, st>>>(ca, cl, pos);
     }
 }
 
