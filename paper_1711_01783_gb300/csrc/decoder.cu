@@ -89,6 +89,11 @@ void decoder_free(mld_decoder *d) {
     if (d->side) cudaStreamDestroy(d->side);
     d->ev_fork = d->ev_join = nullptr;
     d->side = nullptr;
+    for (auto &lg : d->loops) cudaGraphExecDestroy(lg.exec);
+    d->loops.clear();
+    if (d->cap) cudaStreamDestroy(d->cap);
+    d->cap = nullptr;
+    dfree(d->lctr);
 }
 
 // Launch the full decode sequence on device buffers.
@@ -200,6 +205,134 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         int s = syndrome_round(0, false);
         if (s != MLD_OK) return s;
     }
+    // Early termination with the iterations run by the device (a conditional
+    // CUDA-graph loop, see k_loop_cond): layered decoders, and flooding ones
+    // whose syndrome check runs as a pass of its own.  Decoder views without a
+    // capture stream (mld_decode_noalloc) keep the host loop.
+    const bool dev_loop = et && iters > 0 && d->cap && d->lctr && (d->schedule == MLD_SCHED_LAYERED || !fused);
+    if (dev_loop) {
+        // one early-terminated iteration of parity `parity` (l odd: 1), whose
+        // number is lctr[0] + off, enqueued on stream s
+        auto enqueue_half = [&](int parity, int off, cudaStream_t s) -> int {
+            CnArgs c2 = ca;
+            c2.final_pass = 1;
+            c2.fuse = 0;
+            c2.hb1 = d->hb1 + static_cast<size_t>(parity) * h1;
+            if (d->schedule == MLD_SCHED_LAYERED) {
+                CnArgs la = c2;
+                la.col = g->lcol;
+                for (const mld::LayerLaunch &ll : g->layer_launches) {
+                    const mld::CheckClass &k = h.classes[ll.cls];
+                    la.cptr = g->leptr + ll.p0;
+                    const int blocks = std::max(1, std::min(grid_x(static_cast<int64_t>(ll.count) * TPC),
+                                                            sm_count * kLayeredBlocksPerSm));
+                    ClassLaunch cl{k.c0, ll.count, k.dc, k.dc + k.dd, ll.e0, k.s0, blocks};
+                    launch_layered<MsgT, W>(la, cl, g->lchk + ll.p0, slabs, s);
+                }
+                MLD_LAUNCHED("k_check_layered");
+                if (h.n_core > 0) {
+                    k_hard_bits<W><<<dim3(grid_x(static_cast<int64_t>(h.n_core) * (W / 8)), slabs), kBlock, 0, s>>>(
+                        d->Lv, h.n_core, d->hb_core);
+                    MLD_LAUNCHED("k_hard_bits");
+                }
+            } else {
+                if (big < 0) {
+                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(c2, cl, slabs, s, cap_blocks, hard1);
+                } else {
+                    MLD_CUDA(cudaEventRecord(d->ev_fork, s));
+                    MLD_CUDA(cudaStreamWaitEvent(d->side, d->ev_fork, 0));
+                    launch_check_class<MsgT, W>(c2, launches[big], slabs, s, cap_blocks, hard1);
+                    for (size_t i = 0; i < launches.size(); ++i)
+                        if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(c2, launches[i], slabs, d->side, cap_blocks, hard1);
+                    MLD_CUDA(cudaEventRecord(d->ev_join, d->side));
+                    MLD_CUDA(cudaStreamWaitEvent(s, d->ev_join, 0));
+                }
+                MLD_LAUNCHED("k_check_update");
+                if (h.n_core > 0) {
+                    VnArgs v2 = va;
+                    v2.want_bits = 1;
+                    k_var_update<MsgT, W><<<vn_grid, kBlock, 0, s>>>(v2);
+                    MLD_LAUNCHED("k_var_update");
+                }
+            }
+            uint32_t *fcur = d->fail + static_cast<size_t>(parity) * slabs * DW;
+            uint32_t *fnext = d->fail + static_cast<size_t>(1 - parity) * slabs * DW;
+            if (h.n_cn > 0) {
+                SynArgs s2 = sa;
+                s2.et = 1;
+                s2.hb1 = d->hb1 + static_cast<size_t>(parity) * h1;
+                s2.fail = fcur;
+                k_syndrome_check<W><<<syn_grid, kBlock, 0, s>>>(s2);
+                MLD_LAUNCHED("k_syndrome_check");
+            }
+            const int32_t nw = slabs * DW;
+            k_lane_update_dev<W><<<(std::max(batch, nw) + 127) / 128, 128, 0, s>>>(d->done, fcur, fnext, nw, d->iters,
+                                                                                 d->conv, batch, d->lctr, off);
+            MLD_LAUNCHED("k_lane_update");
+            return MLD_OK;
+        };
+        // the loop graph of this batch size, variant and layering (built once)
+        const int variant = (d->schedule == MLD_SCHED_LAYERED ? 2 : 0) + (hard1 ? 1 : 0);
+        cudaGraphExec_t exec = nullptr;
+        for (const auto &lg : d->loops)
+            if (lg.batch == batch && lg.variant == variant && lg.layers_gen == g->layers_gen) exec = lg.exec;
+        if (!exec) {
+            cudaGraph_t gr = nullptr;
+            MLD_CUDA(cudaGraphCreate(&gr, 0));
+            cudaGraphConditionalHandle hnd;
+            cudaError_t e = cudaGraphConditionalHandleCreate(&hnd, gr, 1, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = hnd;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node = nullptr;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &np);
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(d->cap, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(gr);
+                return cuda_fail(e, "device loop: graph set-up");
+            }
+            int s = enqueue_half(1, 1, d->cap);
+            if (s == MLD_OK) s = enqueue_half(0, 2, d->cap);
+            if (s == MLD_OK) {
+                k_loop_cond<W><<<1, 32, 0, d->cap>>>(d->done, slabs * DW, d->lctr, hnd);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) s = cuda_fail(e, "k_loop_cond");
+            }
+            cudaGraph_t body = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(d->cap, &body);
+            if (s == MLD_OK && ec != cudaSuccess) s = cuda_fail(ec, "device loop: capture");
+            if (s == MLD_OK) {
+                e = cudaGraphInstantiate(&exec, gr, 0);
+                if (e != cudaSuccess) s = cuda_fail(e, "device loop: instantiate");
+            }
+            cudaGraphDestroy(gr);
+            if (s != MLD_OK) return s;
+            if (d->loops.size() >= 8) {  // keep the last few batch sizes
+                cudaGraphExecDestroy(d->loops.front().exec);
+                d->loops.erase(d->loops.begin());
+            }
+            d->loops.push_back({batch, variant, g->layers_gen, exec});
+        }
+        {
+            int s = timed_launch(d, kClsLayout, st, "k_loop_init", [&] {
+                k_loop_init<W><<<(slabs * DW + 127) / 128, 128, 0, st>>>(d->done, slabs, batch, d->lctr, iters);
+            });
+            if (s != MLD_OK) return s;
+        }
+        MLD_CUDA(cudaMemsetAsync(d->fail, 0, sizeof(uint32_t) * 2 * slabs * DW, st));
+        d->sample_now = true;
+        {
+            // the whole loop is timed as one region of the check class
+            int s = timed_launch(d, kClsCheck, st, "device loop", [&] { cudaGraphLaunch(exec, st); });
+            if (s != MLD_OK) return s;
+        }
+        iters = 0;  // the host loops below do nothing
+    }
+
     if (d->schedule == MLD_SCHED_LAYERED) {
         // layered schedule: layer after layer, each launch updates messages
         // and posteriors in place; decisions after the last iteration (every
@@ -211,11 +344,16 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
             ca.hb1 = hb1_of(l);
             d->sample_now = ((l - 1) % d->timing_every) == 0;
             int s = timed_launch(d, kClsCheck, st, "k_check_layered", [&] {
+                CnArgs la = ca;
+                la.col = g->lcol;  // layered edge numbering
                 for (const mld::LayerLaunch &ll : g->layer_launches) {
                     const mld::CheckClass &k = h.classes[ll.cls];
-                    ClassLaunch cl{k.c0, ll.count, k.dc, k.dc + k.dd, k.e0, k.s0,
-                                   grid_x(static_cast<int64_t>(ll.count) * TPC)};
-                    launch_layered<MsgT, W>(ca, cl, g->lpos + ll.off, slabs, st);
+                    la.cptr = g->leptr + ll.p0;
+                    // one wave: the kernels loop over the launch's checks
+                    const int blocks = std::max(1, std::min(grid_x(static_cast<int64_t>(ll.count) * TPC),
+                                                            sm_count * kLayeredBlocksPerSm));
+                    ClassLaunch cl{k.c0, ll.count, k.dc, k.dc + k.dd, ll.e0, k.s0, blocks};
+                    launch_layered<MsgT, W>(la, cl, g->lchk + ll.p0, slabs, st);
                 }
             }, static_cast<int>(n_launch));
             if (s != MLD_OK) return s;
@@ -460,7 +598,8 @@ int mld_graph_create(const int32_t *edge_vn, const int32_t *edge_cn, const uint8
 int mld_graph_destroy(mld_graph *g) {
     if (!g) return MLD_OK;
     dfree(g->cptr); dfree(g->col); dfree(g->dptr); dfree(g->vptr); dfree(g->vedge);
-    dfree(g->unit); dfree(g->cint); dfree(g->etype_core); dfree(g->etype_deg1); dfree(g->lpos);
+    dfree(g->unit); dfree(g->cint); dfree(g->etype_core); dfree(g->etype_deg1);
+    dfree(g->lchk); dfree(g->leptr); dfree(g->lcol);
     delete g;
     return MLD_OK;
 }
@@ -483,28 +622,34 @@ int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out) {
 int mld_graph_set_layers(mld_graph *g, const int32_t *layer_of_check, int32_t n_layers) {
     mld::clear_error();
     if (!g) return mld::fail(MLD_EINVAL, "graph_set_layers: null graph");
-    std::vector<mld::LayerLaunch> launches;
-    std::vector<int32_t> pos, user;
-    int32_t nl = 0;
-    int s = mld::build_layers(g->h, layer_of_check, n_layers, &launches, &pos, &user, &nl);
+    mld::LayerTables t;
+    int s = mld::build_layers(g->h, layer_of_check, n_layers, &t);
     if (s != MLD_OK) return s;
     s = check_device(g->device);
     if (s != MLD_OK) return s;
-    int32_t *dpos = nullptr;
-    s = upload(&dpos, pos);
-    if (s != MLD_OK) return s;
-    dfree(g->lpos);
-    g->lpos = dpos;
-    g->layer_launches = std::move(launches);
-    g->layer_user = std::move(user);
-    g->n_layers = nl;
+    int32_t *lchk = nullptr, *leptr = nullptr, *lcol = nullptr;
+    s = upload(&lchk, t.lchk);
+    if (s == MLD_OK) s = upload(&leptr, t.leptr);
+    if (s == MLD_OK) s = upload(&lcol, t.lcol);
+    if (s != MLD_OK) {
+        dfree(lchk); dfree(leptr); dfree(lcol);
+        return s;
+    }
+    dfree(g->lchk); dfree(g->leptr); dfree(g->lcol);
+    g->lchk = lchk;
+    g->leptr = leptr;
+    g->lcol = lcol;
+    g->layer_launches = std::move(t.launches);
+    g->layer_user = std::move(t.layer_user);
+    g->n_layers = t.n_layers;
+    g->layers_gen++;
     return MLD_OK;
 }
 
 int mld_graph_layers_get(const mld_graph *g, int32_t *layer_of_check, int32_t *n_layers) {
     mld::clear_error();
     if (!g || !n_layers) return mld::fail(MLD_EINVAL, "graph_layers_get: null pointer");
-    if (!g->lpos) return mld::fail(MLD_EINVAL, "graph_layers_get: the graph has no layering");
+    if (!g->lchk) return mld::fail(MLD_EINVAL, "graph_layers_get: the graph has no layering");
     *n_layers = g->n_layers;
     if (layer_of_check) std::copy(g->layer_user.begin(), g->layer_user.end(), layer_of_check);
     return MLD_OK;
@@ -543,7 +688,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     }
     int s = check_device(g->device);
     if (s != MLD_OK) return s;
-    if (opts->schedule == MLD_SCHED_LAYERED && !g->lpos) {
+    if (opts->schedule == MLD_SCHED_LAYERED && !g->lchk) {
         // no layering given: the default first fit per check class
         s = mld_graph_set_layers(const_cast<mld_graph *>(g), nullptr, 0);
         if (s != MLD_OK) return s;
@@ -590,6 +735,11 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     if (s == MLD_OK) s = dalloc(&d->post_stage, nb);
     if (s == MLD_OK) s = dalloc(&d->syn_stage, static_cast<size_t>(d->max_batch) * h.n_cn);
     if (s == MLD_OK) s = dalloc(&d->bits_stage, nb);
+    if (s == MLD_OK) s = dalloc(&d->lctr, 2);
+    if (s == MLD_OK) {
+        cudaError_t ce = cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) s = cuda_fail(ce, "decoder_create: capture stream");
+    }
     if (s == MLD_OK) {
         cudaError_t ce = cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking);
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming);

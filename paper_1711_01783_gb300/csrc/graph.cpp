@@ -142,9 +142,7 @@ int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
     return MLD_OK;
 }
 
-int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_layers,
-                 std::vector<LayerLaunch> *launches, std::vector<int32_t> *pos,
-                 std::vector<int32_t> *layer_user, int32_t *n_layers_out) {
+int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_layers, LayerTables *out) {
     const int32_t m = h.n_cn;
     // class of every internal check
     std::vector<int32_t> cls_of(m, 0);
@@ -208,21 +206,28 @@ int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_la
                                             " share a VN of degree >= 2 (check " + std::to_string(h.cuser[ci]) + ")");
             stamp[h.col[e]] = lay[ci];
         }
-    launches->clear();
-    pos->clear();
-    pos->reserve(m);
+    LayerTables t;
+    t.lchk.reserve(m);
+    t.leptr.reserve(static_cast<size_t>(m) + 1);
+    t.lcol.reserve(h.e_core);
     for (int32_t i = 0; i < m; ++i) {
         const int32_t ci = ord[i];
         const CheckClass &cl = h.classes[cls_of[ci]];
         if (cl.dc == 0 && cl.dd == 0) continue;  // nothing to send
-        if (launches->empty() || launches->back().layer != lay[ci] || launches->back().cls != cls_of[ci])
-            launches->push_back(LayerLaunch{lay[ci], cls_of[ci], static_cast<int32_t>(pos->size()), 0});
-        pos->push_back(ci - cl.c0);
-        launches->back().count++;
+        const int32_t p = static_cast<int32_t>(t.lchk.size());
+        const int32_t e = static_cast<int32_t>(t.lcol.size());
+        if (t.launches.empty() || t.launches.back().layer != lay[ci] || t.launches.back().cls != cls_of[ci])
+            t.launches.push_back(LayerLaunch{lay[ci], cls_of[ci], p, 0, e});
+        t.launches.back().count++;
+        t.lchk.push_back(ci);
+        t.leptr.push_back(e);
+        for (int32_t k = h.cptr[ci]; k < h.cptr[ci + 1]; ++k) t.lcol.push_back(h.col[k]);
     }
-    layer_user->assign(m, 0);
-    for (int32_t ci = 0; ci < m; ++ci) (*layer_user)[h.cuser[ci]] = lay[ci];
-    *n_layers_out = nl;
+    t.leptr.push_back(static_cast<int32_t>(t.lcol.size()));
+    t.layer_user.assign(m, 0);
+    for (int32_t ci = 0; ci < m; ++ci) t.layer_user[h.cuser[ci]] = lay[ci];
+    t.n_layers = nl;
+    *out = std::move(t);
     return MLD_OK;
 }
 

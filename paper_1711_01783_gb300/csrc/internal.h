@@ -66,19 +66,25 @@ int build_host_graph(const int32_t *edge_vn, const int32_t *edge_cn,
                      int32_t n_cn, HostGraph *out);
 
 // Layered schedule: the checks of one layer share no core VN.  A layer's
-// checks of one class form one launch; `off` indexes the class positions
-// (j, check c0 + j of the class) of the launch in the graph's layer table.
+// checks of one class form one launch.  Layered decoders number their
+// messages in launch order, so that the messages of a launch are one
+// contiguous run: position p (0 .. checks with edges - 1) is a check in
+// (layer, class, class position) order, lchk[p] its internal id, its core
+// edges the layered edges leptr[p] .. leptr[p+1], lcol[e] the core VN of
+// layered edge e.  A launch covers positions p0 .. p0+count-1 and layered
+// edges e0 .. (one class: e0 + k dc for its k-th check).
 struct LayerLaunch {
-    int32_t layer, cls, off, count;
+    int32_t layer, cls, p0, count, e0;
+};
+struct LayerTables {
+    std::vector<LayerLaunch> launches;
+    std::vector<int32_t> lchk, leptr, lcol, layer_user;
+    int32_t n_layers = 0;
 };
 
 // Validate a layering (layer of every check in the caller's numbering; NULL
-// computes a first fit per class) and build the launch list and the table of
-// class positions, ordered by (layer, class, position).  Every check with
-// edges must be in a register class.
-int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_layers,
-                 std::vector<LayerLaunch> *launches, std::vector<int32_t> *pos,
-                 std::vector<int32_t> *layer_user, int32_t *n_layers_out);
+// computes a first fit per class) and build the layered tables.
+int build_layers(const HostGraph &h, const int32_t *layer_of_check, int32_t n_layers, LayerTables *out);
 
 }  // namespace mld
 
@@ -96,10 +102,11 @@ struct mld_graph {
     // every check with edges is in a register class (posterior accumulation,
     // layered schedule)
     bool acc_ok = false;
-    // layered schedule: launches in order, class positions (device), and the
-    // layer of every check in the caller's numbering
+    // layered schedule: launches in order, the layer of every check in the
+    // caller's numbering, and the device copies of the layered tables
     std::vector<mld::LayerLaunch> layer_launches;
     std::vector<int32_t> layer_user;
     int32_t n_layers = 0;
-    int32_t *lpos = nullptr;
+    int32_t *lchk = nullptr, *leptr = nullptr, *lcol = nullptr;
+    uint64_t layers_gen = 0;  // counts layerings set (device loops record it)
 };

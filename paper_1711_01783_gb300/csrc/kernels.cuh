@@ -665,15 +665,17 @@ void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cuda
 // q = L_v - r_old (Eq. 4 with the current messages), the new r (Eqs. 2-3,
 // as in check_regular) and L_v <- (L_v - r_old) + r_new in place.
 // ---------------------------------------------------------------------------
+// Layered launches number their messages contiguously: the launch's k-th
+// check (internal id c) owns layered edges cl.e0 + k DC ..; a.col is the
+// layered column table.  Its degree-1 slots follow the class order.
 template <typename MsgT, int W, int DC, int DD>
-__device__ __forceinline__ void check_layered(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
-                                              int slab, bool valid) {
+__device__ __forceinline__ void check_layered(const CnArgs &a, const ClassLaunch &cl, int32_t c, int32_t k,
+                                              int lane0, int slab, bool valid) {
     constexpr int D = DC + DD;
     constexpr int F = DecodeFit<MsgT>::value;
     constexpr int NB = W / 8;
-    const int32_t c = cl.c0 + j;
-    const int32_t e0 = cl.e0 + j * DC;
-    const int32_t s0 = cl.s0 + j * DD;
+    const int32_t e0 = cl.e0 + k * DC;
+    const int32_t s0 = cl.s0 + (c - cl.c0) * DD;
     const float lmax = a.lmax, amin = a.amin;
     const uint32_t sb =
         (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >>
@@ -773,30 +775,36 @@ __device__ __forceinline__ void check_layered(const CnArgs &a, const ClassLaunch
     }
 }
 
-// One layer's checks of one class: pos[k] is the class position of the
-// launch's k-th check.  A thread past the end works on the last check and
-// stores nothing (its shuffle pair stays whole).
+// One layer's checks of one class (pos[k]: internal id of the k-th), on a
+// capped grid: a thread keeps its lanes and steps through every stride-th
+// check, so consecutive checks of a wave read consecutive message rows.
+// Both threads of a shuffle pair belong to one check and leave together.
+// Blocks per SM of the layered kernels (72 registers per thread).
+constexpr int kLayeredBlocksPerSm = 7;
+
 template <typename MsgT, int W, int DC, int DD>
-__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6)) k_check_layered(CnArgs a, ClassLaunch cl,
-                                                                                  const int32_t *pos) {
+__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? kLayeredBlocksPerSm : 6))
+    k_check_layered(CnArgs a, ClassLaunch cl, const int32_t *pos) {
     constexpr int TPC = W / kK;
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    int32_t k = static_cast<int32_t>(t / TPC);
-    const bool valid = k < cl.count;
-    if (!valid) k = cl.count - 1;
-    check_layered<MsgT, W, DC, DD>(a, cl, __ldg(pos + k), static_cast<int>(t % TPC) * kK, slab, valid);
+    const int lane0 = static_cast<int>(t % TPC) * kK;
+    const int32_t kstride = static_cast<int32_t>(gridDim.x) * (kBlock / TPC);
+    for (int32_t k = static_cast<int32_t>(t / TPC); k < cl.count; k += kstride)
+        check_layered<MsgT, W, DC, DD>(a, cl, __ldg(pos + k), k, lane0, slab, true);
 }
 
 // Layered update of a check of any degree (edges read through cptr/dptr);
 // leave-one-out sums as total minus own term, as in check_irregular.  Both
 // threads of a shuffle pair belong to one check.
+// a.cptr: the launch's layered edge starts (check k: a.cptr[k] .. a.cptr[k+1]).
 template <typename MsgT, int W>
-__device__ __forceinline__ void check_layered_irregular(const CnArgs &a, int32_t c, int lane0, int slab) {
+__device__ __forceinline__ void check_layered_irregular(const CnArgs &a, int32_t c, int32_t k, int lane0,
+                                                        int slab) {
     constexpr int F = DecodeFit<MsgT>::value;
     constexpr int NB = W / 8;
-    const int32_t e0 = a.cptr[c], e1 = a.cptr[c + 1];
+    const int32_t e0 = a.cptr[k], e1 = a.cptr[k + 1];
     const int32_t s0 = a.dptr[c], s1 = a.dptr[c + 1];
     const int nce = e1 - e0;
     const int deg = nce + (s1 - s0);
@@ -876,9 +884,10 @@ __global__ void __launch_bounds__(kBlock) k_check_layered_irregular(CnArgs a, Cl
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int32_t k = static_cast<int32_t>(t / TPC);
-    if (k >= cl.count) return;  // whole checks, hence whole shuffle pairs
-    check_layered_irregular<MsgT, W>(a, cl.c0 + __ldg(pos + k), static_cast<int>(t % TPC) * kK, slab);
+    const int lane0 = static_cast<int>(t % TPC) * kK;
+    const int32_t kstride = static_cast<int32_t>(gridDim.x) * (kBlock / TPC);
+    for (int32_t k = static_cast<int32_t>(t / TPC); k < cl.count; k += kstride)  // whole checks leave together
+        check_layered_irregular<MsgT, W>(a, __ldg(pos + k), k, lane0, slab);
 }
 
 // The layered schedule is built for the default slab width of each message
@@ -1096,6 +1105,67 @@ template <int W>
 __global__ void k_lane_update(uint32_t *done, const uint32_t *fail, int32_t *iters,
                               uint8_t *conv, int32_t batch, int32_t l, int et) {
     lane_body<W>(done, fail, iters, conv, batch, l, et, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Early termination driven by the device: the iterations run inside a CUDA
+// graph loop (a conditional WHILE node) whose body holds two iterations; the
+// iteration number lives in device memory (lctr[0]: iterations before the
+// body, lctr[1]: the cap), and the loop stops once every codeword has
+// stopped, so no launch runs after the last codeword converges.
+// ---------------------------------------------------------------------------
+// Counter and cap; padding lanes of the last slab count as stopped (so a slab
+// whose real codewords have all stopped is skipped).  done must be zero.
+template <int W>
+__global__ void k_loop_init(uint32_t *done, int32_t slabs, int32_t batch, int32_t *lctr, int32_t max_iters) {
+    constexpr int DW = (W + 31) / 32;
+    constexpr int WB = W >= 32 ? 32 : W;  // lanes per done word
+    constexpr uint32_t full = W >= 32 ? 0xFFFFFFFFu : ((1u << W) - 1u);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        lctr[0] = 0;
+        lctr[1] = max_iters;
+    }
+    if (i < slabs * DW) {
+        const int real = batch - (i / DW) * W - (i % DW) * 32;  // real lanes in this word
+        done[i] = real <= 0 ? full : (real >= WB ? 0u : (full & ~((1u << real) - 1u)));
+    }
+}
+
+// Bookkeeping of iteration l = lctr[0] + off after its syndrome check (fail):
+// as lane_body with early termination, and at the cap every lane stops with
+// the outputs of that iteration.  Also clears the fail words the next
+// iteration uses (fail_next, nwords words).
+template <int W>
+__global__ void k_lane_update_dev(uint32_t *done, const uint32_t *fail, uint32_t *fail_next, int32_t nwords,
+                                  int32_t *iters, uint8_t *conv, int32_t batch, const int32_t *lctr, int32_t off) {
+    constexpr int DW = (W + 31) / 32;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nwords) fail_next[b] = 0u;
+    if (b >= batch) return;
+    const int32_t l = lctr[0] + off;
+    const int slab = b / W, w = b % W;
+    const int word = slab * DW + w / 32;
+    const uint32_t bit = 1u << (w & 31);
+    if (done[word] & bit) return;  // stopped at an earlier iteration
+    const bool ok = (fail[word] & bit) == 0u;
+    iters[b] = l;
+    conv[b] = ok ? 1 : 0;
+    if (ok || l >= lctr[1]) atomicOr(done + word, bit);
+}
+
+// One warp: continue while some lane still iterates, counting the body's two
+// iterations.
+template <int W>
+__global__ void k_loop_cond(const uint32_t *done, int32_t nwords, int32_t *lctr, cudaGraphConditionalHandle h) {
+    constexpr uint32_t full = W >= 32 ? 0xFFFFFFFFu : ((1u << W) - 1u);
+    bool all = true;
+    for (int i = threadIdx.x; i < nwords; i += 32) all = all && (done[i] == full);
+    all = __all_sync(0xFFFFFFFFu, all);
+    if (threadIdx.x == 0) {
+        if (!all) lctr[0] += 2;
+        cudaGraphSetConditional(h, all ? 0u : 1u);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1354,6 +1424,13 @@ struct mld_decoder {
     // posterior accumulation (MLD_VN_ACCUMULATE): two more posterior buffers
     int vn_update = MLD_VN_GATHER;
     int schedule = MLD_SCHED_FLOODING;
+    // early termination run by the device: capture stream, iteration counter
+    // and cap (device), and the loop graphs built so far (per batch size,
+    // variant and layering of the graph)
+    cudaStream_t cap = nullptr;
+    int32_t *lctr = nullptr;
+    struct LoopGraph { int32_t batch, variant; uint64_t layers_gen; cudaGraphExec_t exec; };
+    std::vector<LoopGraph> loops;
     float *Lv2 = nullptr, *Lv3 = nullptr;
     // staging buffers for host pointers
     float *in_stage = nullptr, *sigma_stage = nullptr, *post_stage = nullptr;
