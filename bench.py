@@ -506,18 +506,21 @@ def schedule_comparison(a, dev, barrier, betas=(0.40, 0.42), cap: int = 100, ste
         sig = torch.from_numpy(wl.sigma).to(dev)
         syn = torch.from_numpy(wl.s).to(dev)
         x = torch.from_numpy(wl.x).to(dev)
-        for sched in ("flooding", "layered"):
+        # flooding without soft output checks the syndrome inside the next
+        # check pass (host-driven loop); with soft output, and layered, the
+        # iterations run in the device loop
+        for sched, post in (("flooding", False), ("flooding", True), ("layered", False)):
             dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, schedule=sched)
             holder = {}
 
             def step():
-                holder["o"] = dec.decode_y(y, sig, syn, cap, early_term=True)
+                holder["o"] = dec.decode_y(y, sig, syn, cap, early_term=True, want_post=post)
             for _ in range(2):
                 step()
             ms = time_steps(step, steps, 0, stream, barrier) / steps
             o = holder["o"]
             frame_err = (o["bits"] != x).any(dim=1) | (o["converged"] == 0)
-            res[f"beta{beta}_{sched}"] = {
+            res[f"beta{beta}_{sched}{'_soft' if post else ''}"] = {
                 "ms_per_decode": ms, "value": a.batch * a.n / (ms * 1e-3) / 1e6, "unit": UNIT,
                 "mean_iters": float(o["iters_used"].float().mean()),
                 "max_iters": int(o["iters_used"].max()),
