@@ -442,7 +442,7 @@ def kernel_summary(kt: dict, st: dict, msg: str, batch: int, iters: int, steps: 
 
 
 def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: float,
-               vn_update: str = "gather", schedule: str = "flooding") -> dict:
+               vn_update: str = "gather", schedule: str = "flooding", check_rule: str = "sum_product") -> dict:
     """One more fixed-iteration workload measured like the headline (device-
     resident inputs, CUDA events, max over ranks), with fewer steps."""
     import torch
@@ -453,7 +453,7 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     g = mld.Graph.from_edges(wl.graph)
     if schedule == "layered":
         g.set_layers(None)
-    dec = mld.Decoder(g, a.batch, msg_dtype=msg, vn_update=vn_update, schedule=schedule)
+    dec = mld.Decoder(g, a.batch, msg_dtype=msg, vn_update=vn_update, schedule=schedule, check_rule=check_rule)
     y = torch.from_numpy(wl.y).to(dev)
     sig = torch.from_numpy(wl.sigma).to(dev)
     syn = torch.from_numpy(wl.s).to(dev)
@@ -478,12 +478,47 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     rec = {"value": job_throughput(world, a.batch, a.n, a.sub_steps, ms_max), "unit": UNIT,
            "ms_per_step": ms_max / a.sub_steps, "steps": a.sub_steps, "warmup": 3,
            "rate": rate, "iters": iters, "msg_storage": msg, "vn_update": vn_update, "schedule": schedule,
+           "check_rule": check_rule,
            "gpu_launches": launches,
            "frames_converged": conv, "fer": 1.0 - conv / a.batch}
     rec.update({k: ks[k] for k in ("frac", "frac_decode", "pass_ms", "var_update_ms", "share_check")})
     dec.close()
     g.close()
     return rec
+
+
+def rule_comparison(a, dev, barrier, beta: float = 0.30, cap: int = 100, steps: int = 5) -> dict:
+    """Sum-product against offset min-sum where both decode: rate 0.1,
+    n = 10^6, 64 codewords, early termination (cap 100), flooding schedule."""
+    import torch
+    import paper_1711_01783_gb300 as mld
+    from synthetic import make_workload
+    wl = make_workload(0.1, a.n, a.batch, 2, 8600, beta=beta)
+    g = mld.Graph.from_edges(wl.graph)
+    y = torch.from_numpy(wl.y).to(dev)
+    sig = torch.from_numpy(wl.sigma).to(dev)
+    syn = torch.from_numpy(wl.s).to(dev)
+    x = torch.from_numpy(wl.x).to(dev)
+    stream = torch.cuda.current_stream()
+    res = {"workload": f"rate 0.1, n={a.n}, {a.batch} codewords, beta={beta}, early termination, cap {cap}, "
+                       f"{a.msg} messages, flooding; min-sum offset {mld.DEFAULT_MS_OFFSET} nats"}
+    for rule in ("sum_product", "min_sum"):
+        dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, check_rule=rule)
+        holder = {}
+
+        def step():
+            holder["o"] = dec.decode_y(y, sig, syn, cap, early_term=True, want_post=True)
+        for _ in range(2):
+            step()
+        ms = time_steps(step, steps, 0, stream, barrier) / steps
+        o = holder["o"]
+        frame_err = (o["bits"] != x).any(dim=1) | (o["converged"] == 0)
+        res[rule] = {"ms_per_decode": ms, "value": a.batch * a.n / (ms * 1e-3) / 1e6, "unit": UNIT,
+                     "mean_iters": float(o["iters_used"].float().mean()), "max_iters": int(o["iters_used"].max()),
+                     "fer": float(frame_err.float().mean()), "frames": a.batch}
+        dec.close()
+    g.close()
+    return res
 
 
 def schedule_comparison(a, dev, barrier, betas=(0.40, 0.42), cap: int = 100, steps: int = 5) -> dict:
@@ -673,6 +708,9 @@ def main():
         sub[f"rate{a.rate}_{a.msg}_layered"] = sub_record(a.rate, a.msg, a, rank, dev, dist, barrier, peak,
                                                           "gather", "layered")
         sub["schedules_converging"] = schedule_comparison(a, dev, barrier)
+        sub[f"rate{a.rate}_{a.msg}_minsum"] = sub_record(a.rate, a.msg, a, rank, dev, dist, barrier, peak,
+                                                         check_rule="min_sum")
+        sub["rules_converging"] = rule_comparison(a, dev, barrier)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -194,11 +194,22 @@ int mld_graph_generate(double rate, int32_t n, int32_t d2, uint64_t seed, mld_gr
  *                  (MLD_EINVAL otherwise); if the graph has no layering yet,
  *                  the default one is built here.  Plans (mld_plan_create)
  *                  and mld_decode_noalloc run flooding.
+ *   check_rule : MLD_CHECK_SUM_PRODUCT (0, default): Eqs. 2-3 in the phi form;
+ *                MLD_CHECK_MIN_SUM (1): offset min-sum, an approximation of
+ *                  Eqs. 2-3 that keeps the sign rule (syndrome sign included)
+ *                  and takes as magnitude max(min of the other |q| - ms_offset,
+ *                  0): no phi evaluations, at a cost in frame error rate.
+ *                  Needs the default slab width, the flooding schedule and
+ *                  MLD_VN_GATHER (MLD_EINVAL otherwise).  Plans and
+ *                  mld_decode_noalloc run sum-product.
+ *   ms_offset  : the min-sum offset in nats, >= 0 (ignored by sum-product).
  * Errors: MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA. */
-#define MLD_VN_GATHER      0
-#define MLD_VN_ACCUMULATE  1
-#define MLD_SCHED_FLOODING 0
-#define MLD_SCHED_LAYERED  1
+#define MLD_VN_GATHER         0
+#define MLD_VN_ACCUMULATE     1
+#define MLD_SCHED_FLOODING    0
+#define MLD_SCHED_LAYERED     1
+#define MLD_CHECK_SUM_PRODUCT 0
+#define MLD_CHECK_MIN_SUM     1
 typedef struct {
     int32_t msg_dtype;
     int32_t max_batch;
@@ -206,7 +217,9 @@ typedef struct {
     int32_t slab_width;
     int32_t vn_update;
     int32_t schedule;
-    int32_t reserved[10];  /* must be zero */
+    int32_t check_rule;
+    float ms_offset;
+    int32_t reserved[8];  /* must be zero */
 } mld_opts;
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out);
 int mld_decoder_destroy(mld_decoder *d);

@@ -14,6 +14,13 @@ cycle-free graphs, the one-sweep closed form of a repetition chain, the
 order-invariance of checks that share no VN, the coset symmetry, exhaustive
 ML and the noiseless limit (``tests/test_oracle_layered.py``).
 
+Offset min-sum (``decode_ms``): the flooding decoder with the check update's
+magnitude replaced by the smallest other magnitude minus an offset.  Pinned
+by the exact degree-2 chain (offset 0), the single-check bound
+|r_min-sum| >= |r_sum-product| with equal signs, the offset's closed form on
+one check, the coset symmetry, exhaustive ML, the noiseless limit and
+planted mistakes (``tests/test_oracle_minsum.py``).
+
 Weighted BP (``wbp``): forward plus a hand-written reverse-mode gradient,
 pinned by central finite differences of its own FP64 loss and by the
 all-weights-one case equalling plain BP.
@@ -73,6 +80,9 @@ def _load():
             lib.oracle_decode_layered.restype = ctypes.c_int
             lib.oracle_decode_layered.argtypes = [i32, i32, i64, ptr, ptr, ptr, i32, ptr, ptr,
                                                   i32, i32, dbl, ptr, ptr, ptr, ptr, i32]
+            lib.oracle_decode_ms.restype = ctypes.c_int
+            lib.oracle_decode_ms.argtypes = [i32, i32, i64, ptr, ptr, dbl, i32, ptr, ptr,
+                                             i32, i32, dbl, ptr, ptr, ptr, ptr, i32]
             lib.oracle_wbp.restype = ctypes.c_int
             lib.oracle_wbp.argtypes = [i32, i32, i64, ptr, ptr, ptr, i32, i32, ptr, ptr, ptr, i32, ptr, dbl,
                                        ptr, ptr, ptr, ptr, i32]
@@ -158,6 +168,29 @@ def decode_layered(graph, llr: np.ndarray, syndrome: np.ndarray, iters: int, ord
                                        int(threads or default_threads()))
     if st != 0:
         raise RuntimeError(f"oracle_decode_layered failed with status {st}")
+    return dict(post=post, bits=bits, converged=conv, iters_used=used)
+
+
+def decode_ms(graph, llr: np.ndarray, syndrome: np.ndarray, iters: int, offset: float = 0.0,
+              early_term: bool = False, lmax: float = LMAX, threads: int | None = None):
+    """Offset min-sum in FP64 (flooding schedule): the check update keeps the
+    sign rule and takes max(min of the other |q| - offset, 0) as magnitude.
+    Same inputs and outputs as :func:`decode`."""
+    n, m, ev, ec = _edges(graph)
+    L = np.ascontiguousarray(np.atleast_2d(llr), dtype=np.float64)
+    S = np.ascontiguousarray(np.atleast_2d(syndrome), dtype=np.uint8)
+    B = L.shape[0]
+    if L.shape != (B, n) or S.shape != (B, m):
+        raise ValueError("shape mismatch")
+    post = np.zeros((B, n), dtype=np.float64)
+    bits = np.zeros((B, n), dtype=np.uint8)
+    conv = np.zeros(B, dtype=np.uint8)
+    used = np.zeros(B, dtype=np.int32)
+    st = _load().oracle_decode_ms(n, m, ev.shape[0], _p(ev), _p(ec), float(offset), B, _p(L), _p(S),
+                                  int(iters), int(bool(early_term)), float(lmax),
+                                  _p(post), _p(bits), _p(conv), _p(used), int(threads or default_threads()))
+    if st != 0:
+        raise RuntimeError(f"oracle_decode_ms failed with status {st}")
     return dict(post=post, bits=bits, converged=conv, iters_used=used)
 
 

@@ -132,6 +132,7 @@ typedef struct {
     int next;                /* work counter (atomic) */
     int status;
     const int32_t *order;    /* layered schedule: the check order [n_cn] */
+    double ms_offset;        /* offset min-sum: the offset subtracted from the minimum */
 } decode_job;
 
 static int decode_one(const decode_job *J, int b) {
@@ -249,7 +250,7 @@ int oracle_decode(int32_t n_vn, int32_t n_cn, int64_t n_edges,
     int st = adj_build(&a, n_vn, n_cn, n_edges, edge_vn, edge_cn);
     if (st != ORACLE_OK) return st;
     decode_job J = {&a, llr, syndrome, batch, max_iters, early_term, lmax,
-                    post, bits, converged, iters_used, 0, ORACLE_OK, NULL};
+                    post, bits, converged, iters_used, 0, ORACLE_OK, NULL, 0.0};
     st = run_workers(decode_worker, &J, n_threads, batch);
     adj_free(&a);
     return st != ORACLE_OK ? st : J.status;
@@ -377,8 +378,116 @@ int oracle_decode_layered(int32_t n_vn, int32_t n_cn, int64_t n_edges,
     int st = adj_build(&a, n_vn, n_cn, n_edges, edge_vn, edge_cn);
     if (st != ORACLE_OK) return st;
     decode_job J = {&a, llr, syndrome, batch, max_iters, early_term, lmax,
-                    post, bits, converged, iters_used, 0, ORACLE_OK, order};
+                    post, bits, converged, iters_used, 0, ORACLE_OK, order, 0.0};
     st = run_workers(decode_layered_worker, &J, n_threads, batch);
+    adj_free(&a);
+    return st != ORACLE_OK ? st : J.status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Offset min-sum, one codeword (flooding schedule).                          */
+/*                                                                           */
+/* The approximation of the check update that keeps the sign rule of Eqs. 2-3 */
+/* and replaces the magnitude phi(sum phi(|q|)) by the smallest magnitude     */
+/* among the other incoming messages, reduced by an offset and floored at 0:  */
+/*   r_{c->v} = (1-2 s_c) prod_{v' in R_c \ v} sgn q_{v'->c}                  */
+/*              * max( min_{v' in R_c \ v} |q_{v'->c}| - offset, 0 )          */
+/* (the paper's closing remark on simplifying the check update in the LLR     */
+/* domain; the offset is a parameter).  Everything else (clamps, Eq. 4,       */
+/* Eq. 5, Step 5) is as in the sum-product decoder above.                     */
+/* ------------------------------------------------------------------------- */
+static int decode_one_ms(const decode_job *J, int b) {
+    const adjacency *a = J->a;
+    const int32_t n = a->n_vn;
+    const int64_t E = a->n_edges;
+    const double lmax = J->lmax;
+    const double *llr = J->llr + (size_t)b * n;
+    const uint8_t *s = J->syn + (size_t)b * a->n_cn;
+    double *Lch = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *L = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *q = malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    double *r = malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    uint8_t *xhat = malloc((size_t)(n > 0 ? n : 1));
+    if (!Lch || !L || !q || !r || !xhat) {
+        free(Lch); free(L); free(q); free(r); free(xhat);
+        return ORACLE_ENOMEM;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        Lch[v] = clampd(llr[v], -lmax, lmax);
+        L[v] = Lch[v];
+        xhat[v] = L[v] < 0.0;
+    }
+    for (int64_t e = 0; e < E; ++e) r[e] = 0.0;
+    int used = 0, conv = 0;
+    for (int l = 1; l <= J->max_iters; ++l) {
+        /* Eq. 4 */
+        for (int32_t v = 0; v < n; ++v)
+            for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) {
+                double acc = Lch[v];
+                for (int64_t k2 = a->vptr[v]; k2 < a->vptr[v + 1]; ++k2)
+                    if (k2 != k) acc += r[a->vedge[k2]];
+                q[a->vedge[k]] = clampd(acc, -lmax, lmax);
+            }
+        /* offset min-sum check update */
+        for (int32_t c = 0; c < a->n_cn; ++c)
+            for (int64_t k = a->cptr[c]; k < a->cptr[c + 1]; ++k) {
+                double sgn = (s[c] & 1) ? -1.0 : 1.0;
+                double mn = lmax;   /* |q| <= lmax: the minimum of an empty set is lmax */
+                for (int64_t k2 = a->cptr[c]; k2 < a->cptr[c + 1]; ++k2) {
+                    if (k2 == k) continue;
+                    const double qe = q[a->cedge[k2]];
+                    if (qe < 0.0) sgn = -sgn;
+                    if (fabs(qe) < mn) mn = fabs(qe);
+                }
+                const double mag = mn - J->ms_offset > 0.0 ? mn - J->ms_offset : 0.0;
+                r[a->cedge[k]] = sgn * mag;
+            }
+        /* Eq. 5 */
+        for (int32_t v = 0; v < n; ++v) {
+            double acc = Lch[v];
+            for (int64_t k = a->vptr[v]; k < a->vptr[v + 1]; ++k) acc += r[a->vedge[k]];
+            L[v] = acc;
+            xhat[v] = acc < 0.0;
+        }
+        used = l;
+        if (J->early_term && syndrome_ok(a, xhat, s)) { conv = 1; break; }
+    }
+    if (!conv) conv = syndrome_ok(a, xhat, s);
+    if (J->post) memcpy(J->post + (size_t)b * n, L, sizeof(double) * (size_t)n);
+    memcpy(J->bits + (size_t)b * n, xhat, (size_t)n);
+    J->converged[b] = (uint8_t)conv;
+    J->iters_used[b] = used;
+    free(Lch); free(L); free(q); free(r); free(xhat);
+    return ORACLE_OK;
+}
+
+static void *decode_ms_worker(void *arg) {
+    decode_job *J = arg;
+    for (;;) {
+        int b = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (b >= J->batch) break;
+        int st = decode_one_ms(J, b);
+        if (st != ORACLE_OK) __atomic_store_n(&J->status, st, __ATOMIC_RELAXED);
+    }
+    return NULL;
+}
+
+int oracle_decode_ms(int32_t n_vn, int32_t n_cn, int64_t n_edges,
+                     const int32_t *edge_vn, const int32_t *edge_cn, double offset,
+                     int32_t batch, const double *llr, const uint8_t *syndrome,
+                     int32_t max_iters, int32_t early_term, double lmax,
+                     double *post, uint8_t *bits, uint8_t *converged,
+                     int32_t *iters_used, int32_t n_threads) {
+    if (n_vn < 0 || n_cn < 0 || n_edges < 0 || batch < 0 || max_iters < 0 || !(lmax > 0.0) || !(offset >= 0.0))
+        return ORACLE_EINVAL;
+    if (batch == 0) return ORACLE_OK;
+    if (!llr || !syndrome || !bits || !converged || !iters_used) return ORACLE_EINVAL;
+    adjacency a;
+    int st = adj_build(&a, n_vn, n_cn, n_edges, edge_vn, edge_cn);
+    if (st != ORACLE_OK) return st;
+    decode_job J = {&a, llr, syndrome, batch, max_iters, early_term, lmax,
+                    post, bits, converged, iters_used, 0, ORACLE_OK, NULL, offset};
+    st = run_workers(decode_ms_worker, &J, n_threads, batch);
     adj_free(&a);
     return st != ORACLE_OK ? st : J.status;
 }

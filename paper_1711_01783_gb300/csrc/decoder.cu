@@ -144,7 +144,10 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     // early termination without soft output: degree-1 decisions only, and
     // the syndrome of iteration l-1 formed inside check pass l (every check
     // in a register class; otherwise a separate syndrome check per iteration)
-    const bool hard1 = et && !post;
+    ca.rule = d->check_rule == MLD_CHECK_MIN_SUM ? kRuleMinSum : kRuleSumProduct;
+    ca.ms_off = d->ms_off_i;
+    // (the decision-only form is a sum-product property)
+    const bool hard1 = et && !post && d->check_rule == MLD_CHECK_SUM_PRODUCT;
     const bool fused = hard1 && g->fusable;
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
@@ -658,8 +661,13 @@ int mld_graph_layers_get(const mld_graph *g, int32_t *layer_of_check, int32_t *n
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out) {
     mld::clear_error();
     if (!g || !opts || !out) return mld::fail(MLD_EINVAL, "decoder_create: null pointer");
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < 8; ++i)
         if (opts->reserved[i] != 0) return mld::fail(MLD_EINVAL, "decoder_create: reserved field not zero");
+    if (opts->check_rule != MLD_CHECK_SUM_PRODUCT && opts->check_rule != MLD_CHECK_MIN_SUM)
+        return mld::fail(MLD_EINVAL, "decoder_create: unknown check_rule");
+    if (opts->check_rule == MLD_CHECK_MIN_SUM &&
+        (!(opts->ms_offset >= 0.f) || !std::isfinite(opts->ms_offset)))
+        return mld::fail(MLD_EINVAL, "decoder_create: ms_offset must be finite and >= 0");
     if (opts->vn_update != MLD_VN_GATHER && opts->vn_update != MLD_VN_ACCUMULATE)
         return mld::fail(MLD_EINVAL, "decoder_create: unknown vn_update");
     if (opts->schedule != MLD_SCHED_FLOODING && opts->schedule != MLD_SCHED_LAYERED)
@@ -679,6 +687,11 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
             return mld::fail(MLD_EINVAL, "decoder_create: posterior accumulation needs every check to have at "
                                          "most 8 edges and at most one degree-1 VN");
     }
+    if (opts->check_rule == MLD_CHECK_MIN_SUM &&
+        (W != ((opts->msg_dtype == MLD_MSG_F16) ? 64 : 32) || opts->schedule != MLD_SCHED_FLOODING ||
+         opts->vn_update != MLD_VN_GATHER))
+        return mld::fail(MLD_EINVAL, "decoder_create: min-sum needs the default slab width, the flooding "
+                                     "schedule and MLD_VN_GATHER");
     if (opts->schedule == MLD_SCHED_LAYERED) {
         if (W != ((opts->msg_dtype == MLD_MSG_F16) ? 64 : 32))
             return mld::fail(MLD_EINVAL, "decoder_create: the layered schedule needs the default slab width");
@@ -701,6 +714,8 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     d->W = W;
     d->vn_update = opts->vn_update;
     d->schedule = opts->schedule;
+    d->check_rule = opts->check_rule;
+    d->ms_off_i = opts->check_rule == MLD_CHECK_MIN_SUM ? opts->ms_offset * 1.4426950408889634f : 0.f;
     d->max_batch = opts->max_batch;
     d->max_slabs = (opts->max_batch + W - 1) / W;
     set_units(d, opts->lmax > 0.f ? opts->lmax : 25.f);

@@ -250,7 +250,13 @@ struct CnArgs {
     // entry and L_v of this iteration (Eq. 4) once the pass is complete.
     // Null: the variable update gathers the messages instead.
     float *acc;
+    // Check rule: 0 sum-product (Eqs. 2-3), 1 offset min-sum with offset
+    // ms_off (internal units).
+    int rule;
+    float ms_off;
 };
+
+enum { kRuleSumProduct = 0, kRuleMinSum = 1 };
 
 template <typename MsgT, int W>
 __device__ __forceinline__ void emit_deg1(const CnArgs &a, int slab, int slot, int lane0,
@@ -627,8 +633,15 @@ __global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, Cla
 // (fixed iterations, default slab width, register classes only) the kernels
 // also add every new message to the next posteriors.
 template <typename MsgT, int W>
+void launch_minsum_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks);
+
+template <typename MsgT, int W>
 void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks,
                         bool hard1) {
+    if (ca.rule == kRuleMinSum) {
+        launch_minsum_class<MsgT, W>(ca, cl, slabs, st, cap_blocks);
+        return;
+    }
     const dim3 grid(cl.blocks, slabs);
     const dim3 capped(std::max(1, std::min(cl.blocks, cap_blocks)), slabs);
     const dim3 g = (cl.dc >= 0 && cl.deg <= 6) ? capped : grid;
@@ -913,6 +926,203 @@ void launch_layered(const CnArgs &ca, const ClassLaunch &cl, const int32_t *pos,
         }
 #undef MLD_LCASE
         k_check_layered_irregular<MsgT, W><<<grid, kBlock, 0, st>>>(ca, cl, pos);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Offset min-sum check update: the sign rule of Eqs. 2-3 (syndrome sign
+// included) with magnitude max(min of the other |q| - offset, 0), |q| clamped
+// at lmax.  The two smallest magnitudes and the position of the smallest give
+// every leave-one-out minimum.
+// ---------------------------------------------------------------------------
+template <typename MsgT, int W, int DC, int DD>
+__device__ __forceinline__ void check_minsum(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
+                                             int slab) {
+    constexpr int D = DC + DD;
+    constexpr int NB = W / 8;
+    const int32_t c = cl.c0 + j;
+    const int32_t e0 = cl.e0 + j * DC;
+    const int32_t s0 = cl.s0 + j * DD;
+    const float lmax = a.lmax, off = a.ms_off;
+    const uint32_t sb =
+        (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >>
+         (lane0 & 7));
+    const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
+    MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
+    const float *lvb = a.Lv + static_cast<size_t>(slab) * a.n_core * W + lane0;
+    const float *l1b = a.lch1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
+    float m1[kK], m2[kK];
+    uint32_t par[kK], neg[kK], at[kK];
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) {
+        par[kk] = (sb >> kk) & 1u;
+        neg[kk] = 0u;
+        at[kk] = 0u;
+        m1[kk] = lmax;
+        m2[kk] = lmax;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float4 q;
+        if (i < DC) {
+            const float4 lv = ldf4(lvb + static_cast<size_t>(__ldg(a.col + e0 + i)) * W);
+            const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
+            q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
+        } else {
+            q = ldf4(l1b + static_cast<size_t>(s0 + i - DC) * W);  // degree-1 VN: q = L_ch
+        }
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) {
+            const float qk = f4get(q, kk);
+            const uint32_t ng = qk < 0.f ? 1u : 0u;
+            par[kk] ^= ng;
+            neg[kk] |= ng << i;
+            const float mg = fminf(fabsf(qk), lmax);
+            const bool lt1 = mg < m1[kk];
+            m2[kk] = lt1 ? m1[kk] : fminf(m2[kk], mg);
+            at[kk] = lt1 ? static_cast<uint32_t>(i) : at[kk];
+            m1[kk] = lt1 ? mg : m1[kk];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        if (i < DC || a.final_pass) {
+            float4 rv;
+#pragma unroll
+            for (int kk = 0; kk < kK; ++kk) {
+                const float mg = fmaxf((at[kk] == static_cast<uint32_t>(i) ? m2[kk] : m1[kk]) - off, 0.f);
+                const uint32_t sg = (par[kk] ^ (neg[kk] >> i)) & 1u;
+                f4set(rv, kk, sg ? -mg : mg);
+            }
+            if (i < DC) {
+                MsgT *rp = rb + static_cast<size_t>(e0 + i) * W;
+                if (a.et) store_r<MsgT, W>(a, rp, rv, donenib);
+                else Msg<MsgT>::store(rp, rv);
+            } else {
+                emit_deg1<MsgT, W>(a, slab, s0 + i - DC, lane0, rv, donenib, true);
+            }
+        }
+    }
+}
+
+// Any degree (edges through cptr/dptr): the same rule over two passes.
+template <typename MsgT, int W>
+__device__ __forceinline__ void check_minsum_irregular(const CnArgs &a, int32_t c, int lane0, int slab) {
+    constexpr int NB = W / 8;
+    const int32_t e0 = a.cptr[c], e1 = a.cptr[c + 1];
+    const int32_t s0 = a.dptr[c], s1 = a.dptr[c + 1];
+    const int nce = e1 - e0;
+    const int deg = nce + (s1 - s0);
+    const float lmax = a.lmax, off = a.ms_off;
+    const uint32_t sb =
+        (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >>
+         (lane0 & 7));
+    const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
+    MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
+    const float *lvb = a.Lv + static_cast<size_t>(slab) * a.n_core * W + lane0;
+    const float *l1b = a.lch1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
+    auto input = [&](int i) -> float4 {
+        if (i < nce) {
+            const float4 lv = ldf4(lvb + static_cast<size_t>(__ldg(a.col + e0 + i)) * W);
+            const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
+            return make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
+        }
+        return ldf4(l1b + static_cast<size_t>(s0 + i - nce) * W);
+    };
+    float m1[kK], m2[kK];
+    uint32_t par[kK];
+    int at[kK];
+#pragma unroll
+    for (int kk = 0; kk < kK; ++kk) {
+        par[kk] = (sb >> kk) & 1u;
+        at[kk] = -1;
+        m1[kk] = lmax;
+        m2[kk] = lmax;
+    }
+    for (int i = 0; i < deg; ++i) {
+        const float4 q = input(i);
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) {
+            const float qk = f4get(q, kk);
+            par[kk] ^= qk < 0.f ? 1u : 0u;
+            const float mg = fminf(fabsf(qk), lmax);
+            if (mg < m1[kk]) {
+                m2[kk] = m1[kk];
+                m1[kk] = mg;
+                at[kk] = i;
+            } else {
+                m2[kk] = fminf(m2[kk], mg);
+            }
+        }
+    }
+    for (int i = 0; i < deg; ++i) {
+        const bool out_core = i < nce;
+        if (!out_core && !a.final_pass) continue;
+        const float4 q = input(i);
+        float4 rv;
+#pragma unroll
+        for (int kk = 0; kk < kK; ++kk) {
+            const float mg = fmaxf((at[kk] == i ? m2[kk] : m1[kk]) - off, 0.f);
+            const uint32_t sg = par[kk] ^ (f4get(q, kk) < 0.f ? 1u : 0u);
+            f4set(rv, kk, sg ? -mg : mg);
+        }
+        if (out_core)
+            store_r<MsgT, W>(a, rb + static_cast<size_t>(e0 + i) * W, rv, donenib);
+        else
+            emit_deg1<MsgT, W>(a, slab, s0 + i - nce, lane0, rv, donenib, true);
+    }
+}
+
+// Min-sum launches loop over their checks on a capped grid (the state per
+// thread is small, so every shape loops).  Both threads of a shuffle pair
+// belong to one check and leave together.  80 registers: the loads of a
+// check's terms are all in flight at once.
+constexpr int kMinSumBlocksPerSm = 6;
+template <typename MsgT, int W, int DC, int DD>
+__global__ void __launch_bounds__(kBlock, kMinSumBlocksPerSm) k_check_minsum(CnArgs a, ClassLaunch cl) {
+    constexpr int TPC = W / kK;
+    const int slab = blockIdx.y;
+    if (a.et && slab_all_done<W>(a.done, slab)) return;
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int lane0 = static_cast<int>(t % TPC) * kK;
+    const int32_t jstride = static_cast<int32_t>(gridDim.x) * (kBlock / TPC);
+    for (int32_t j = static_cast<int32_t>(t / TPC); j < cl.count; j += jstride)
+        check_minsum<MsgT, W, DC, DD>(a, cl, j, lane0, slab);
+}
+
+template <typename MsgT, int W>
+__global__ void __launch_bounds__(kBlock) k_check_minsum_irregular(CnArgs a, ClassLaunch cl) {
+    constexpr int TPC = W / kK;
+    const int slab = blockIdx.y;
+    if (a.et && slab_all_done<W>(a.done, slab)) return;
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int lane0 = static_cast<int>(t % TPC) * kK;
+    const int32_t jstride = static_cast<int32_t>(gridDim.x) * (kBlock / TPC);
+    for (int32_t j = static_cast<int32_t>(t / TPC); j < cl.count; j += jstride)
+        check_minsum_irregular<MsgT, W>(a, cl.c0 + j, lane0, slab);
+}
+
+// Offset min-sum is built for the default slab width of each message type.
+template <typename MsgT, int W>
+void launch_minsum_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks) {
+    if constexpr (kAccWidth<MsgT, W>) {
+        const dim3 g(std::max(1, std::min(cl.blocks, cap_blocks)), slabs);
+        const int dd = cl.deg - cl.dc;
+#define MLD_MCASE(DCV, DDV)                                                   \
+    case (DCV) * 2 + (DDV):                                                   \
+        k_check_minsum<MsgT, W, DCV, DDV><<<g, kBlock, 0, st>>>(ca, cl);      \
+        return;
+        if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
+            switch (cl.dc * 2 + dd) {
+                MLD_MCASE(1, 0) MLD_MCASE(2, 0) MLD_MCASE(3, 0) MLD_MCASE(4, 0)
+                MLD_MCASE(5, 0) MLD_MCASE(6, 0) MLD_MCASE(7, 0) MLD_MCASE(8, 0)
+                MLD_MCASE(0, 1) MLD_MCASE(1, 1) MLD_MCASE(2, 1) MLD_MCASE(3, 1)
+                MLD_MCASE(4, 1) MLD_MCASE(5, 1) MLD_MCASE(6, 1) MLD_MCASE(7, 1)
+                default: break;
+            }
+        }
+#undef MLD_MCASE
+        k_check_minsum_irregular<MsgT, W><<<g, kBlock, 0, st>>>(ca, cl);
     }
 }
 
@@ -1424,6 +1634,8 @@ struct mld_decoder {
     // posterior accumulation (MLD_VN_ACCUMULATE): two more posterior buffers
     int vn_update = MLD_VN_GATHER;
     int schedule = MLD_SCHED_FLOODING;
+    int check_rule = MLD_CHECK_SUM_PRODUCT;
+    float ms_off_i = 0.f;  // min-sum offset, internal units
     // early termination run by the device: capture stream, iteration counter
     // and cap (device), and the loop graphs built so far (per batch size,
     // variant and layering of the graph)

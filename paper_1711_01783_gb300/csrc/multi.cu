@@ -475,8 +475,8 @@ int validate_jobs(const mld_job *jobs, int32_t n_jobs, uint32_t flags, int *devi
         if (jb.decoder->device != dev) return mld::fail(MLD_EINVAL, at + "decoder belongs to another device");
         if (jb.batch < 1 || jb.batch > jb.decoder->max_batch) return mld::fail(MLD_EINVAL, at + "batch out of range");
         if (jb.max_iters < 0) return mld::fail(MLD_EINVAL, at + "negative max_iters");
-        if (jb.decoder->schedule != MLD_SCHED_FLOODING)
-            return mld::fail(MLD_EINVAL, at + "plans run the flooding schedule (layered decoder given)");
+        if (jb.decoder->schedule != MLD_SCHED_FLOODING || jb.decoder->check_rule != MLD_CHECK_SUM_PRODUCT)
+            return mld::fail(MLD_EINVAL, at + "plans run flooding sum-product (layered or min-sum decoder given)");
         const mld::HostGraph &h = jb.decoder->g->h;
         if ((h.n_vn > 0 && (!jb.in || !jb.bits_out)) || (h.n_cn > 0 && !jb.syndrome) || !jb.converged ||
             !jb.iters_used)
