@@ -148,7 +148,9 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     ca.ms_off = d->ms_off_i;
     // (the decision-only form is a sum-product property)
     const bool hard1 = et && !post && d->check_rule == MLD_CHECK_SUM_PRODUCT;
-    const bool fused = hard1 && g->fusable;
+    // the fused syndrome check is for the host-driven loop (decoder views
+    // without a capture stream); otherwise the device loop runs the iterations
+    const bool fused = hard1 && g->fusable && !d->cap;
     VnArgs va{g->vptr, g->vedge, h.n_core, h.e_core, d->r, d->lch, d->Lv, d->hb_core, d->done, 0, et ? 1 : 0};
     SynArgs sa{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, d->sbits, d->hb_core, d->hb1,
                d->fail, d->done, et ? 1 : 0, batch};
@@ -209,9 +211,9 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         if (s != MLD_OK) return s;
     }
     // Early termination with the iterations run by the device (a conditional
-    // CUDA-graph loop, see k_loop_cond): layered decoders, and flooding ones
-    // whose syndrome check runs as a pass of its own.  Decoder views without a
-    // capture stream (mld_decode_noalloc) keep the host loop.
+    // CUDA-graph loop, see k_loop_cond), so no launch follows the iteration at
+    // which the last codeword stops.  Decoder views without a capture stream
+    // (mld_decode_noalloc) keep the host loop.
     const bool dev_loop = et && iters > 0 && d->cap && d->lctr && (d->schedule == MLD_SCHED_LAYERED || !fused);
     if (dev_loop) {
         // one early-terminated iteration of parity `parity` (l odd: 1), whose
