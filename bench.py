@@ -487,6 +487,39 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     return rec
 
 
+def md_frontend(a, dev, peak: float, steps: int = 10) -> dict:
+    """Multidimensional-reconciliation kernels on the benchmark's shape
+    (64 x 10^6 samples): bytes each must move (Bob: y, bits in; alpha, |y|
+    out = 9.5 B per sample; Alice: x, alpha, |y| in, LLR out = 12.5 B per
+    sample) over their CUDA-event time."""
+    import torch
+    import paper_1711_01783_gb300 as mld
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    x = torch.randn((a.batch, a.n), device=dev, generator=g)
+    y = x + 0.8 * torch.randn((a.batch, a.n), device=dev, generator=g)
+    bits = torch.randint(0, 2, (a.batch, a.n), device=dev, dtype=torch.uint8, generator=g)
+    nv = torch.full((a.batch,), 0.64, device=dev)
+    out = {}
+    for name, fn, per in (("bob", lambda: mld.md_bob(y, bits), 9.5),
+                          ("alice", lambda: mld.md_alice(x, al, yn, nv), 12.5)):
+        if name == "alice":
+            al, yn = mld.md_bob(y, bits)
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        gbs = per * a.batch * a.n / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "GB/s": gbs, "frac": gbs / peak, "bytes_per_sample": per,
+                     "Msamples/s": a.batch * a.n / (ms * 1e-3) / 1e6}
+    return out
+
+
 def rule_comparison(a, dev, barrier, beta: float = 0.30, cap: int = 100, steps: int = 5) -> dict:
     """Sum-product against offset min-sum where both decode: rate 0.1,
     n = 10^6, 64 codewords, early termination (cap 100), flooding schedule."""
@@ -711,6 +744,7 @@ def main():
         sub[f"rate{a.rate}_{a.msg}_minsum"] = sub_record(a.rate, a.msg, a, rank, dev, dist, barrier, peak,
                                                          check_rule="min_sum")
         sub["rules_converging"] = rule_comparison(a, dev, barrier)
+        sub["md_frontend"] = md_frontend(a, dev, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -426,6 +426,34 @@ int mld_decode_noalloc(const mld_graph *g, int32_t msg_dtype, const float *llr,
                        uint32_t flags, uint8_t *bits_out, float *post_out,
                        uint8_t *converged, int32_t *iters_used, void *stream);
 
+/* ---- multidimensional reconciliation front end (d = 8) --------------------
+ * The step before decoding in the paper's reconciliation (Results,
+ * "Information reconciliation for CV-QKD system"; Fig. 1): Bob's and Alice's
+ * correlated Gaussian samples y = x + z become Bob's bits and Alice's LLRs of
+ * them by rotating blocks of 8 samples onto a virtual binary-input AWGN
+ * channel (the paper cites the method; these are its definitions).  A_i is
+ * the matrix of left multiplication by the basis octonion e_i, octonions
+ * being pairs of quaternions (1, i, j, k) with the Cayley-Dickson product
+ * (a, b)(c, d) = (ac - conj(d) b, da + b conj(c)).
+ * mld_md_bob: per block of 8 samples y and 8 bits b (uint8 0/1, the bits
+ *   Bob will send the syndrome of): ynorm = |y|, u = (1 - 2b)/sqrt 8,
+ *   alpha_i = <A_i y/|y|, u>, so that M = sum_i alpha_i A_i is orthogonal and
+ *   M y/|y| = u.  A block of zeros is taken as direction e_0.
+ *   y: float [count], bits: uint8 [count], alpha_out: float [count] (8 per
+ *   block), ynorm_out: float [count/8]; count a multiple of 8.
+ * mld_md_alice: LLR_k = 2 |y| (M x)_k / (sqrt 8 sigma_z^2) per block (the
+ *   LLR of Bob's bit on the virtual channel; for Gaussian modulation only the
+ *   noise variance sigma_z^2 of y = x + z enters), for `rows` rows of
+ *   `row_len` samples (a multiple of 8), e.g. [codeword][n], with one noise
+ *   variance per row: x, alpha, llr_out float [rows][row_len], ynorm
+ *   [rows][row_len/8], noise_var [rows].  The LLRs feed mld_decode.
+ * All pointers are device memory; y, x, alpha and outputs 16-byte aligned,
+ * bits 8-byte aligned (MLD_EINVAL otherwise).  Errors: MLD_EINVAL, MLD_ECUDA. */
+int mld_md_bob(const float *y, const uint8_t *bits, int64_t count, float *alpha_out, float *ynorm_out,
+               void *stream);
+int mld_md_alice(const float *x, const float *alpha, const float *ynorm, const float *noise_var, int32_t rows,
+                 int64_t row_len, float *llr_out, void *stream);
+
 /* ---- phi evaluation (verification hook) ----------------------------------
  * Evaluates on the device the float phi(x) = -ln tanh(x/2) that the check
  * update uses (the LLR-domain message map that the closing paragraph of the

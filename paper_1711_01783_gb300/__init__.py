@@ -43,7 +43,7 @@ EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destr
            "mld_decoder_timing_read", "mld_decode_noalloc", "mld_plan_create", "mld_plan_launch",
            "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_wbp_forward", "mld_wbp_backward",
            "mld_tape_destroy", "mld_phi_eval", "mld_ensemble_size", "mld_ensemble_edges",
-           "mld_graph_generate", "mld_graph_set_layers", "mld_graph_layers_get")
+           "mld_graph_generate", "mld_graph_set_layers", "mld_graph_layers_get", "mld_md_bob", "mld_md_alice")
 
 
 class MldError(RuntimeError):
@@ -118,6 +118,8 @@ def _load() -> ctypes.CDLL:
         "mld_wbp_backward": (ctypes.c_int, [P, P, P, P, P]),
         "mld_tape_destroy": (ctypes.c_int, [P]),
         "mld_phi_eval": (ctypes.c_int, [I32, P, P, I64, P]),
+        "mld_md_bob": (ctypes.c_int, [P, P, I64, P, P, P]),
+        "mld_md_alice": (ctypes.c_int, [P, P, P, P, I32, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -548,6 +550,41 @@ def decode_noalloc(graph: Graph, llr, syndrome, iters: int, msg_dtype: str = "f3
     return out
 
 
+def md_bob(y, bits, stream=None):
+    """Bob's side of multidimensional reconciliation (mld_md_bob): CUDA float32
+    y [..., 8k] and uint8 bits of the same shape -> (alpha [..., 8k], |y| [..., k])."""
+    torch = _torch()
+    if not (_is_cuda_tensor(y) and _is_cuda_tensor(bits)):
+        raise TypeError("md_bob takes CUDA tensors")
+    y = y.contiguous().to(torch.float32)
+    bits = bits.contiguous().to(torch.uint8)
+    if y.shape != bits.shape or y.shape[-1] % 8:
+        raise ValueError("y and bits must have one shape whose last dimension is a multiple of 8")
+    alpha = torch.empty_like(y)
+    ynorm = torch.empty(y.shape[:-1] + (y.shape[-1] // 8,), dtype=torch.float32, device=y.device)
+    _check(lib().mld_md_bob(_ptr(y), _ptr(bits), y.numel(), _ptr(alpha), _ptr(ynorm), _stream_handle(stream)))
+    return alpha, ynorm
+
+
+def md_alice(x, alpha, ynorm, noise_var, stream=None):
+    """Alice's LLRs of Bob's bits (mld_md_alice): CUDA float32 x, alpha
+    [rows, n], ynorm [rows, n/8], noise_var [rows] -> LLR [rows, n]."""
+    torch = _torch()
+    if not all(_is_cuda_tensor(t) for t in (x, alpha, ynorm, noise_var)):
+        raise TypeError("md_alice takes CUDA tensors")
+    x = x.contiguous().to(torch.float32)
+    alpha = alpha.contiguous().to(torch.float32)
+    ynorm = ynorm.contiguous().to(torch.float32)
+    noise_var = noise_var.contiguous().to(torch.float32).reshape(-1)
+    if x.dim() != 2 or alpha.shape != x.shape or x.shape[1] % 8 or tuple(ynorm.shape) != (x.shape[0], x.shape[1] // 8) \
+            or noise_var.shape[0] != x.shape[0]:
+        raise ValueError("x, alpha [rows, n], ynorm [rows, n/8], noise_var [rows]")
+    llr = torch.empty_like(x)
+    _check(lib().mld_md_alice(_ptr(x), _ptr(alpha), _ptr(ynorm), _ptr(noise_var), x.shape[0], x.shape[1],
+                              _ptr(llr), _stream_handle(stream)))
+    return llr
+
+
 def phi(x, msg_dtype: str = "f32", stream=None):
     """Device phi(x) = -ln tanh(x/2) as used by the check update of a decoder
     with the given message storage type (float32 CUDA tensor in and out)."""
@@ -560,5 +597,6 @@ def phi(x, msg_dtype: str = "f32", stream=None):
 
 
 __all__ = ["Graph", "Decoder", "Plan", "Tape", "weighted_bp", "phi", "decode_noalloc", "ensemble_edges",
+           "md_bob", "md_alice", "DEFAULT_MS_OFFSET",
            "ENSEMBLE_CORE_FRAC", "version", "lib", "MldError", "EXPORTS",
            "LIB_PATH", "NOALLOC_SCRATCH_BYTES"]
