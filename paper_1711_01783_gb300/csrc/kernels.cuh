@@ -1075,8 +1075,10 @@ __device__ __forceinline__ void check_minsum_irregular(const CnArgs &a, int32_t 
 
 // Min-sum launches loop over their checks on a capped grid (the state per
 // thread is small, so every shape loops).  Both threads of a shuffle pair
-// belong to one check and leave together.
-constexpr int kMinSumBlocksPerSm = 8;
+// belong to one check and leave together.  80 registers: the loads of a
+// check's terms are all in flight at once (64 registers spill: 0.37 -> 0.51 ms
+// per pass at rate 0.1, n = 10^6, 64 codewords).
+constexpr int kMinSumBlocksPerSm = 6;
 template <typename MsgT, int W, int DC, int DD>
 __global__ void __launch_bounds__(kBlock, kMinSumBlocksPerSm) k_check_minsum(CnArgs a, ClassLaunch cl) {
     constexpr int TPC = W / kK;
