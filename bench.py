@@ -520,6 +520,45 @@ def md_frontend(a, dev, peak: float, steps: int = 10) -> dict:
     return out
 
 
+def peg_record(dev, n: int = 4096, frames: int = 256, beta: float = 0.42, cap: int = 80) -> dict:
+    """PEG construction of the rate-0.1 family on the host (mld_peg_edges)
+    and what it buys: frame error rate of the PEG code and of the socket-
+    permutation code of the same degrees on the same kind of channel, decoded
+    on the GPU (float messages, early termination)."""
+    import torch
+    import paper_1711_01783_gb300 as mld
+    from synthetic import biawgn_observe, bob_syndrome, preset_graph, random_bits, sigma_for_beta
+    from types import SimpleNamespace
+    rate, core, d2 = 0.1, 0.2, 20
+    n_c = int(round(core * n))
+    deg = np.zeros((3, n), np.int64)
+    deg[0, :n_c] = 3
+    deg[0, :int(round(0.4 * n_c))] = 2
+    deg[1, :n_c] = d2
+    deg[2, n_c:] = 1
+    m1, m2 = n_c - int(round(rate * n)), n - n_c
+    mask = np.concatenate([np.full(m1, 1), np.full(m2, 6)])
+    t0 = time.perf_counter()
+    ev, ec, et = mld.peg_edges(deg, mask, np.random.default_rng(1).permutation(m1 + m2))
+    t_peg = time.perf_counter() - t0
+    graphs = {"peg": SimpleNamespace(n_vn=n, n_cn=m1 + m2, edge_vn=ev, edge_cn=ec, edge_type=et),
+              "socket": preset_graph(rate, n, 1)}
+    sig = sigma_for_beta(rate, beta)
+    res = {"n": n, "edges": int(ev.shape[0]), "construction_s": t_peg,
+           "construction_kedges_per_s": ev.shape[0] / t_peg / 1e3,
+           "fer_workload": f"{frames} frames, beta={beta}, cap {cap}, early termination, f32"}
+    for name, g in graphs.items():
+        x = random_bits(frames, n, 77)
+        s = bob_syndrome(g, x)
+        y = biawgn_observe(x, sig, 77)
+        G = mld.Graph.from_edges(g)
+        out = mld.Decoder(G, frames, msg_dtype="f32").decode_y(
+            torch.from_numpy(y).to(dev), torch.full((frames,), sig, device=dev), torch.from_numpy(s).to(dev),
+            cap, early_term=True)
+        res[f"fer_{name}"] = 1.0 - float(out["converged"].float().mean())
+    return res
+
+
 def rule_comparison(a, dev, barrier, beta: float = 0.30, cap: int = 100, steps: int = 5) -> dict:
     """Sum-product against offset min-sum where both decode: rate 0.1,
     n = 10^6, 64 codewords, early termination (cap 100), flooding schedule."""
@@ -745,6 +784,7 @@ def main():
                                                          check_rule="min_sum")
         sub["rules_converging"] = rule_comparison(a, dev, barrier)
         sub["md_frontend"] = md_frontend(a, dev, peak)
+        sub["peg"] = peg_record(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

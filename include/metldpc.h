@@ -156,6 +156,30 @@ int mld_ensemble_edges(double rate, int32_t n, int32_t d2, double core_frac, uin
                        int32_t *edge_vn, int32_t *edge_cn, uint8_t *edge_type, int64_t capacity);
 int mld_graph_generate(double rate, int32_t n, int32_t d2, uint64_t seed, mld_graph **out);
 
+/* ---- progressive edge growth (PEG) ----------------------------------------
+ * mld_peg_edges: the edge list of a multi-edge-type Tanner graph built by
+ * progressive edge growth from VN degrees per edge type (the paper's codes
+ * are PEG-built from multi-edge-type degree distributions, Results and
+ * Table 1).  Host only.
+ *   deg        : host int32 [n_types][n_vn], edges of each type per VN.
+ *   mask       : host uint32 [n_cn]; bit t set if check c accepts type t.
+ *   prio       : host int32 [n_cn] tie-break priorities, or NULL (index).
+ *   outputs    : edge_vn, edge_cn int32 and edge_type uint8 [capacity] (>=
+ *                the total degree), in placement order; *n_edges the count.
+ * Rule: VNs in order of increasing total degree (ties by index), each VN's
+ * edges type by type; an edge of type t goes to a check accepting t that is
+ * not yet a neighbour of the VN, among the farthest from it in the graph
+ * built so far (unreachable ones if any, else those at the largest
+ * breadth-first level, the VN's neighbours being level 1), and among those
+ * the lowest current degree, then the lowest priority.  Each placement costs
+ * one breadth-first search (stopped once every check accepting t is
+ * reached), so construction time grows with the square of the edge count.
+ * Errors: MLD_EINVAL (arguments, capacity, more than 2^30 edges, 1 <= n_types
+ * <= MLD_MAX_EDGE_TYPES), MLD_EGRAPH (no check left for an edge). */
+int mld_peg_edges(int32_t n_vn, int32_t n_types, const int32_t *deg, int32_t n_cn, const uint32_t *mask,
+                  const int32_t *prio, int64_t capacity, int32_t *edge_vn, int32_t *edge_cn,
+                  uint8_t *edge_type, int64_t *n_edges);
+
 /* ---- decoder --------------------------------------------------------------
  * mld_decoder_create: allocate the device state for decoding up to
  * opts->max_batch codewords of graph g at once.  The graph must outlive the

@@ -43,7 +43,7 @@ EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destr
            "mld_decoder_timing_read", "mld_decode_noalloc", "mld_plan_create", "mld_plan_launch",
            "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_wbp_forward", "mld_wbp_backward",
            "mld_tape_destroy", "mld_phi_eval", "mld_ensemble_size", "mld_ensemble_edges",
-           "mld_graph_generate", "mld_graph_set_layers", "mld_graph_layers_get", "mld_md_bob", "mld_md_alice")
+           "mld_graph_generate", "mld_graph_set_layers", "mld_graph_layers_get", "mld_md_bob", "mld_md_alice", "mld_peg_edges")
 
 
 class MldError(RuntimeError):
@@ -119,6 +119,7 @@ def _load() -> ctypes.CDLL:
         "mld_tape_destroy": (ctypes.c_int, [P]),
         "mld_phi_eval": (ctypes.c_int, [I32, P, P, I64, P]),
         "mld_md_bob": (ctypes.c_int, [P, P, I64, P, P, P]),
+        "mld_peg_edges": (ctypes.c_int, [I32, I32, P, I32, P, P, I64, P, P, P, ctypes.POINTER(I64)]),
         "mld_md_alice": (ctypes.c_int, [P, P, P, P, I32, I64, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -190,6 +191,30 @@ def ensemble_edges(rate: float, n: int, d2: int, seed: int, core_frac: float | N
     _check(lib().mld_ensemble_edges(float(rate), int(n), int(d2), cf, int(seed), _ptr(ev), _ptr(ec), _ptr(et),
                                     e.value))
     return ev, ec, et, int(m.value)
+
+
+def peg_edges(deg, mask, prio=None):
+    """Progressive-edge-growth edge list (mld_peg_edges, host only).
+
+    deg: int [n_types, n_vn] edges per type and VN; mask: int [n_cn] (bit t:
+    the check accepts type t); prio: int [n_cn] tie-break priorities or None.
+    Returns (edge_vn int32, edge_cn int32, edge_type uint8) in placement order.
+    """
+    d = np.ascontiguousarray(deg, dtype=np.int32)
+    if d.ndim != 2:
+        raise ValueError("deg must be [n_types, n_vn]")
+    m = np.ascontiguousarray(mask, dtype=np.uint32)
+    p = None if prio is None else np.ascontiguousarray(prio, dtype=np.int32)
+    if p is not None and p.shape != m.shape:
+        raise ValueError("prio must be [n_cn]")
+    total = int(d.astype(np.int64).sum())
+    ev = np.empty(total, np.int32)
+    ec = np.empty(total, np.int32)
+    et = np.empty(total, np.uint8)
+    k = ctypes.c_int64()
+    _check(lib().mld_peg_edges(d.shape[1], d.shape[0], _ptr(d), m.shape[0], _ptr(m), _ptr(p), total,
+                               _ptr(ev), _ptr(ec), _ptr(et), ctypes.byref(k)))
+    return ev[:k.value], ec[:k.value], et[:k.value]
 
 
 class Graph:
@@ -597,6 +622,6 @@ def phi(x, msg_dtype: str = "f32", stream=None):
 
 
 __all__ = ["Graph", "Decoder", "Plan", "Tape", "weighted_bp", "phi", "decode_noalloc", "ensemble_edges",
-           "md_bob", "md_alice", "DEFAULT_MS_OFFSET",
+           "md_bob", "md_alice", "DEFAULT_MS_OFFSET", "peg_edges",
            "ENSEMBLE_CORE_FRAC", "version", "lib", "MldError", "EXPORTS",
            "LIB_PATH", "NOALLOC_SCRATCH_BYTES"]

@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmetldpc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["decoder.cu", "multi.cu", "wbp.cu", "md.cu", "graph.cpp", "ensemble.cpp"]
+SOURCES = ["decoder.cu", "multi.cu", "wbp.cu", "md.cu", "graph.cpp", "ensemble.cpp", "peg.cpp"]
 
 
 def nvcc() -> str:
