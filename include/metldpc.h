@@ -46,7 +46,9 @@ extern "C" {
 #define MLD_EINVAL   (-1)  /* bad argument (null pointer, size, flag, dtype)   */
 #define MLD_ENOMEM   (-2)  /* host or device allocation failed                  */
 #define MLD_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed        */
-#define MLD_ETIMEOUT (-4)  /* a bounded device-side wait gave up                 */
+#define MLD_ETIMEOUT (-4)  /* reserved for a bounded device-side wait that gives
+                              up; no entry point waits on the device, so none
+                              returns it                                      */
 #define MLD_EGRAPH   (-5)  /* malformed Tanner graph (index out of range, ...)   */
 
 /* ---- edge-message storage type (mld_opts.msg_dtype) ---------------------- */
@@ -106,6 +108,21 @@ typedef struct {
     int32_t max_vn_deg;
 } mld_graph_stats;
 int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out);
+
+/* The graph store's device index arrays, for tools that inspect or verify it
+ * (device pointers into the library's own memory, int32, valid until
+ * mld_graph_destroy).  Internal numbering: core edges check-major (cptr
+ * [n_cn + 1], col [e_core]: core VN of each edge), degree-1 slots (dptr
+ * [n_cn + 1]), the VN-major view (vptr [n_core + 1], vedge [e_core]), the
+ * internal index of every caller VN (unit [n_vn]) and every caller check's
+ * internal index (cint [n_cn]).  Writing through them corrupts the graph:
+ * decoders created with `checked` detect that before decoding.  Errors:
+ * MLD_EINVAL. */
+typedef struct {
+    const int32_t *cptr, *col, *dptr, *vptr, *vedge, *unit, *cint;
+    int64_t n_cptr, n_col, n_dptr, n_vptr, n_vedge, n_unit, n_cint;
+} mld_index_arrays;
+int mld_graph_index_arrays(const mld_graph *g, mld_index_arrays *out);
 
 /* ---- layers for the layered (serial) schedule -----------------------------
  * The layered schedule updates the checks one after another, each from the
@@ -227,6 +244,15 @@ int mld_peg_edges(int32_t n_vn, int32_t n_types, const int32_t *deg, int32_t n_c
  *                  MLD_VN_GATHER (MLD_EINVAL otherwise).  Plans and
  *                  mld_decode_noalloc run sum-product.
  *   ms_offset  : the min-sum offset in nats, >= 0 (ignored by sum-product).
+ *   checked    : 0 (default) or 1: before every decode call a kernel checks
+ *                every index of the graph's device arrays (and the layered
+ *                tables of a layered decoder) against its range; the call
+ *                waits for that check (it is no longer asynchronous) and, if
+ *                the store is corrupted, returns MLD_EGRAPH naming the array,
+ *                index and value without launching any decoding kernel.
+ *                The result is kept for mld_decode_status.  A debugging aid
+ *                for programs that may write stray device memory; plans do
+ *                not check.
  * Errors: MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA. */
 #define MLD_VN_GATHER         0
 #define MLD_VN_ACCUMULATE     1
@@ -243,7 +269,8 @@ typedef struct {
     int32_t schedule;
     int32_t check_rule;
     float ms_offset;
-    int32_t reserved[8];  /* must be zero */
+    int32_t checked;
+    int32_t reserved[7];  /* must be zero */
 } mld_opts;
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out);
 int mld_decoder_destroy(mld_decoder *d);
@@ -290,8 +317,11 @@ int mld_decode_y(mld_decoder *d, const float *y, const float *sigma,
                  uint32_t flags, uint8_t *bits_out, float *post_out,
                  uint8_t *converged, int32_t *iters_used, void *stream);
 
-/* Status of device-detected errors for work already completed on the stream
- * (MLD_OK if none).  Synchronizes nothing; call after the stream is idle. */
+/* Status of the device-side check of the last decode call of a decoder
+ * created with `checked` (MLD_OK if the graph store was intact, or for other
+ * decoders); on a corrupted store, MLD_EGRAPH with the array, index and value
+ * in mld_last_error().  Reads the decoder's device status word with a
+ * blocking copy; call after the stream is idle. */
 int mld_decode_status(mld_decoder *d);
 
 /* ---- uneven batches: several graphs in one launch --------------------------

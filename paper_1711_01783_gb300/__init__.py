@@ -43,7 +43,7 @@ EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destr
            "mld_decoder_timing_read", "mld_decode_noalloc", "mld_plan_create", "mld_plan_launch",
            "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_wbp_forward", "mld_wbp_backward",
            "mld_tape_destroy", "mld_phi_eval", "mld_ensemble_size", "mld_ensemble_edges",
-           "mld_graph_generate", "mld_graph_set_layers", "mld_graph_layers_get", "mld_md_bob", "mld_md_alice", "mld_peg_edges")
+           "mld_graph_generate", "mld_graph_set_layers", "mld_graph_layers_get", "mld_md_bob", "mld_md_alice", "mld_peg_edges", "mld_graph_index_arrays")
 
 
 class MldError(RuntimeError):
@@ -63,7 +63,12 @@ class Opts(ctypes.Structure):
                 ("lmax", ctypes.c_float), ("slab_width", ctypes.c_int32),
                 ("vn_update", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("check_rule", ctypes.c_int32), ("ms_offset", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("checked", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class IndexArrays(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in ("cptr", "col", "dptr", "vptr", "vedge", "unit", "cint")] + \
+               [(f"n_{f}", ctypes.c_int64) for f in ("cptr", "col", "dptr", "vptr", "vedge", "unit", "cint")]
 
 
 class Timing(ctypes.Structure):
@@ -120,6 +125,7 @@ def _load() -> ctypes.CDLL:
         "mld_phi_eval": (ctypes.c_int, [I32, P, P, I64, P]),
         "mld_md_bob": (ctypes.c_int, [P, P, I64, P, P, P]),
         "mld_peg_edges": (ctypes.c_int, [I32, I32, P, I32, P, P, I64, P, P, P, ctypes.POINTER(I64)]),
+        "mld_graph_index_arrays": (ctypes.c_int, [P, ctypes.POINTER(IndexArrays)]),
         "mld_md_alice": (ctypes.c_int, [P, P, P, P, I32, I64, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -271,6 +277,13 @@ class Graph:
             raise ValueError("layer_of_check must be [n_cn]")
         _check(lib().mld_graph_set_layers(self._h, _ptr(lay), int(lay.max(initial=-1)) + 1))
 
+    def index_arrays(self) -> dict:
+        """Device pointers and lengths of the store's index arrays
+        (mld_graph_index_arrays)."""
+        ia = IndexArrays()
+        _check(lib().mld_graph_index_arrays(self._h, ctypes.byref(ia)))
+        return {f: getattr(ia, f) for f, _ in IndexArrays._fields_}
+
     def layers(self):
         """(layer_of_check int32 [n_cn], n_layers) of the current layering."""
         n = ctypes.c_int32()
@@ -308,7 +321,7 @@ class Decoder:
     def __init__(self, graph: Graph, max_batch: int, msg_dtype: str = "f32",
                  lmax: float = 25.0, slab_width: int = 0, vn_update: str = "gather",
                  schedule: str = "flooding", check_rule: str = "sum_product",
-                 ms_offset: float = DEFAULT_MS_OFFSET):
+                 ms_offset: float = DEFAULT_MS_OFFSET, checked: bool = False):
         o = Opts()
         o.msg_dtype = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
         o.max_batch = int(max_batch)
@@ -318,6 +331,7 @@ class Decoder:
         o.schedule = {"flooding": MLD_SCHED_FLOODING, "layered": MLD_SCHED_LAYERED}[schedule]
         o.check_rule = {"sum_product": MLD_CHECK_SUM_PRODUCT, "min_sum": MLD_CHECK_MIN_SUM}[check_rule]
         o.ms_offset = float(ms_offset) if check_rule == "min_sum" else 0.0
+        o.checked = 1 if checked else 0
         h = ctypes.c_void_p()
         _check(lib().mld_decoder_create(graph.handle, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -78,6 +78,8 @@ void decoder_free(mld_decoder *d) {
     dfree(d->Lv2); dfree(d->Lv3);
     dfree(d->hb_core); dfree(d->hb1); dfree(d->sbits);
     dfree(d->done); dfree(d->fail); dfree(d->iters); dfree(d->conv); dfree(d->status);
+    if (d->status_host) cudaFreeHost(d->status_host);
+    d->status_host = nullptr;
     dfree(d->in_stage); dfree(d->sigma_stage); dfree(d->post_stage);
     dfree(d->syn_stage); dfree(d->bits_stage);
     for (auto &t : d->timed) { d->event_pool.push_back(t.a); d->event_pool.push_back(t.b); }
@@ -482,6 +484,43 @@ const void *mapped_host(const void *p) {
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
+const char *array_name(int id) {
+    static const char *names[] = {"?", "cptr", "col", "dptr", "vptr", "vedge", "unit", "cint", "lchk", "leptr",
+                                  "lcol"};
+    return (id >= 1 && id <= 10) ? names[id] : names[0];
+}
+
+std::string graph_fault_text(const int32_t st[4]) {
+    return std::string("graph store corrupted on the device: ") + array_name(st[1]) + "[" + std::to_string(st[2]) +
+           "] holds " + std::to_string(st[3]) + ", out of its range";
+}
+
+// Checked decoders: validate the graph store on the device, wait for the
+// result, and refuse to decode a corrupted store (no decode kernel runs).
+int validate_store(mld_decoder *d, cudaStream_t st) {
+    const mld_graph *g = d->g;
+    const mld::HostGraph &h = g->h;
+    MLD_CUDA(cudaMemsetAsync(d->status, 0, 4 * sizeof(int32_t), st));
+    const bool lay = d->schedule == MLD_SCHED_LAYERED && g->lchk;
+    ValidateArgs va{g->cptr, g->col, g->dptr, g->vptr, g->vedge, g->unit, g->cint,
+                    lay ? g->lchk : nullptr, lay ? g->leptr : nullptr, lay ? g->lcol : nullptr,
+                    h.n_vn, h.n_cn, h.n_core, h.n_deg1, h.e_core,
+                    0, d->status};
+    if (lay) {
+        int32_t np = 0;
+        for (const mld::LayerLaunch &ll : g->layer_launches) np += ll.count;
+        va.n_lpos = np;
+    }
+    int64_t top = std::max<int64_t>({static_cast<int64_t>(h.e_core), static_cast<int64_t>(h.n_vn) + 1,
+                                     static_cast<int64_t>(h.n_cn) + 1, static_cast<int64_t>(va.n_lpos) + 1});
+    k_validate_graph<<<static_cast<int>(std::min<int64_t>((top + kBlock - 1) / kBlock, 152 * 16)), kBlock, 0, st>>>(va);
+    MLD_LAUNCHED("k_validate_graph");
+    MLD_CUDA(cudaMemcpyAsync(d->status_host, d->status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MLD_CUDA(cudaStreamSynchronize(st));
+    if (d->status_host[0] != 0) return mld::fail(d->status_host[0], graph_fault_text(d->status_host));
+    return MLD_OK;
+}
+
 int decode_common(mld_decoder *d, const float *in, const float *sigma, const uint8_t *syndrome,
                   int32_t batch, int32_t max_iters, uint32_t flags, uint8_t *bits_out,
                   float *post_out, uint8_t *converged, int32_t *iters_used, void *stream,
@@ -501,6 +540,10 @@ int decode_common(mld_decoder *d, const float *in, const float *sigma, const uin
     int s = check_device(d->device);
     if (s != MLD_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (d->checked && d->status_host) {
+        s = validate_store(d, st);
+        if (s != MLD_OK) return s;
+    }
     const bool dev = (flags & MLD_DEVICE_PTRS) != 0;
     const bool et = (flags & MLD_EARLY_TERM) != 0;
     const size_t nb = static_cast<size_t>(batch) * h.n_vn;
@@ -624,6 +667,20 @@ int mld_graph_stats_get(const mld_graph *g, mld_graph_stats *out) {
     return MLD_OK;
 }
 
+int mld_graph_index_arrays(const mld_graph *g, mld_index_arrays *out) {
+    mld::clear_error();
+    if (!g || !out) return mld::fail(MLD_EINVAL, "graph_index_arrays: null pointer");
+    const mld::HostGraph &h = g->h;
+    out->cptr = g->cptr;   out->n_cptr = h.n_cn + 1;
+    out->col = g->col;     out->n_col = h.e_core;
+    out->dptr = g->dptr;   out->n_dptr = h.n_cn + 1;
+    out->vptr = g->vptr;   out->n_vptr = h.n_core + 1;
+    out->vedge = g->vedge; out->n_vedge = h.e_core;
+    out->unit = g->unit;   out->n_unit = h.n_vn;
+    out->cint = g->cint;   out->n_cint = h.n_cn;
+    return MLD_OK;
+}
+
 int mld_graph_set_layers(mld_graph *g, const int32_t *layer_of_check, int32_t n_layers) {
     mld::clear_error();
     if (!g) return mld::fail(MLD_EINVAL, "graph_set_layers: null graph");
@@ -663,8 +720,9 @@ int mld_graph_layers_get(const mld_graph *g, int32_t *layer_of_check, int32_t *n
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out) {
     mld::clear_error();
     if (!g || !opts || !out) return mld::fail(MLD_EINVAL, "decoder_create: null pointer");
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 7; ++i)
         if (opts->reserved[i] != 0) return mld::fail(MLD_EINVAL, "decoder_create: reserved field not zero");
+    if (opts->checked != 0 && opts->checked != 1) return mld::fail(MLD_EINVAL, "decoder_create: checked must be 0 or 1");
     if (opts->check_rule != MLD_CHECK_SUM_PRODUCT && opts->check_rule != MLD_CHECK_MIN_SUM)
         return mld::fail(MLD_EINVAL, "decoder_create: unknown check_rule");
     if (opts->check_rule == MLD_CHECK_MIN_SUM &&
@@ -717,6 +775,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     d->vn_update = opts->vn_update;
     d->schedule = opts->schedule;
     d->check_rule = opts->check_rule;
+    d->checked = opts->checked != 0;
     d->ms_off_i = opts->check_rule == MLD_CHECK_MIN_SUM ? opts->ms_offset * 1.4426950408889634f : 0.f;
     d->max_batch = opts->max_batch;
     d->max_slabs = (opts->max_batch + W - 1) / W;
@@ -746,7 +805,15 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     if (s == MLD_OK) s = dalloc(&d->fail, 2 * S * DW);  // two buffers (iteration parity) for plans
     if (s == MLD_OK) s = dalloc(&d->iters, S * W);
     if (s == MLD_OK) s = dalloc(&d->conv, S * W);
-    if (s == MLD_OK) s = dalloc(&d->status, 1);
+    if (s == MLD_OK) s = dalloc(&d->status, 4);
+    if (s == MLD_OK && d->checked) {
+        cudaError_t ce = cudaHostAlloc(reinterpret_cast<void **>(&d->status_host), 4 * sizeof(int32_t),
+                                       cudaHostAllocDefault);
+        if (ce != cudaSuccess) {
+            d->status_host = nullptr;
+            s = cuda_fail(ce, "decoder_create: status word");
+        }
+    }
     if (s == MLD_OK) s = dalloc(&d->in_stage, nb);
     if (s == MLD_OK) s = dalloc(&d->sigma_stage, static_cast<size_t>(d->max_batch));
     if (s == MLD_OK) s = dalloc(&d->post_stage, nb);
@@ -764,7 +831,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
         if (ce != cudaSuccess) s = cuda_fail(ce, "decoder_create: side stream");
     }
     if (s == MLD_OK) {
-        cudaError_t e2 = cudaMemset(d->status, 0, sizeof(int32_t));
+        cudaError_t e2 = cudaMemset(d->status, 0, 4 * sizeof(int32_t));
         if (e2 != cudaSuccess) s = cuda_fail(e2, "cudaMemset");
     }
     if (s != MLD_OK) {
@@ -800,10 +867,10 @@ int mld_decode_y(mld_decoder *d, const float *y, const float *sigma, const uint8
 int mld_decode_status(mld_decoder *d) {
     mld::clear_error();
     if (!d) return mld::fail(MLD_EINVAL, "decode_status: null decoder");
-    int32_t v = 0;
-    cudaError_t e = cudaMemcpy(&v, d->status, sizeof(v), cudaMemcpyDeviceToHost);
+    int32_t v[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(v, d->status, sizeof(v), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "decode_status");
-    return v == 0 ? MLD_OK : mld::fail(v, "device-detected error");
+    return v[0] == 0 ? MLD_OK : mld::fail(v[0], graph_fault_text(v));
 }
 
 int mld_decoder_timing_enable(mld_decoder *d, int enable) {

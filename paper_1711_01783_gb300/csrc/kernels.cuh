@@ -1380,6 +1380,69 @@ __global__ void k_loop_cond(const uint32_t *done, int32_t nwords, int32_t *lctr,
 }
 
 // ---------------------------------------------------------------------------
+// Graph store validation (decoders created with `checked`): every index of
+// the device arrays is compared with its range, reading each array only
+// within its own length.  The first violation found is recorded in st[0..3]:
+// status code, array id, index, value (st[0] is claimed with a compare-and-
+// swap, so concurrent finders leave one record).
+// ---------------------------------------------------------------------------
+struct ValidateArgs {
+    const int32_t *cptr, *col, *dptr, *vptr, *vedge, *unit, *cint;
+    const int32_t *lchk, *leptr, *lcol;  // layered tables or null
+    int32_t n_vn, n_cn, n_core, n_deg1, e_core, n_lpos;
+    int32_t *st;
+};
+
+enum { kArrCptr = 1, kArrCol, kArrDptr, kArrVptr, kArrVedge, kArrUnit, kArrCint, kArrLchk, kArrLeptr, kArrLcol };
+
+__device__ __forceinline__ void flag_bad(int32_t *st, int arr, int64_t i, int32_t v) {
+    if (atomicCAS(st, 0, MLD_EGRAPH) == 0) {
+        st[1] = arr;
+        st[2] = static_cast<int32_t>(i);
+        st[3] = v;
+    }
+}
+
+// ptr[0 .. n] must rise from 0 to `last`
+__device__ __forceinline__ void check_ptr(const int32_t *ptr, int64_t n, int32_t last, int64_t i, int arr,
+                                          int32_t *st) {
+    if (i > n) return;
+    const int32_t v = ptr[i];
+    const bool bad = (i == 0 && v != 0) || (i == n && v != last) || (i < n && v > ptr[i + 1]) || v < 0 || v > last;
+    if (bad) flag_bad(st, arr, i, v);
+}
+
+__device__ __forceinline__ void check_range(const int32_t *a, int64_t n, int32_t hi, int64_t i, int arr,
+                                            int32_t *st) {
+    if (i >= n) return;
+    const int32_t v = a[i];
+    if (v < 0 || v >= hi) flag_bad(st, arr, i, v);
+}
+
+__global__ void __launch_bounds__(kBlock) k_validate_graph(ValidateArgs a) {
+    // every array's last index: e_core - 1, n_vn - 1, n_cn, n_core (<= n_vn), n_lpos
+    int64_t top = a.e_core;
+    top = top > static_cast<int64_t>(a.n_vn) + 1 ? top : static_cast<int64_t>(a.n_vn) + 1;
+    top = top > static_cast<int64_t>(a.n_cn) + 1 ? top : static_cast<int64_t>(a.n_cn) + 1;
+    top = top > static_cast<int64_t>(a.n_lpos) + 1 ? top : static_cast<int64_t>(a.n_lpos) + 1;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < top; i += stride) {
+        check_ptr(a.cptr, a.n_cn, a.e_core, i, kArrCptr, a.st);
+        check_range(a.col, a.e_core, a.n_core, i, kArrCol, a.st);
+        check_ptr(a.dptr, a.n_cn, a.n_deg1, i, kArrDptr, a.st);
+        check_ptr(a.vptr, a.n_core, a.e_core, i, kArrVptr, a.st);
+        check_range(a.vedge, a.e_core, a.e_core, i, kArrVedge, a.st);
+        check_range(a.unit, a.n_vn, a.n_vn, i, kArrUnit, a.st);
+        check_range(a.cint, a.n_cn, a.n_cn, i, kArrCint, a.st);
+        if (a.lchk) {
+            check_range(a.lchk, a.n_lpos, a.n_cn, i, kArrLchk, a.st);
+            check_ptr(a.leptr, a.n_lpos, a.e_core, i, kArrLeptr, a.st);
+            check_range(a.lcol, a.e_core, a.n_core, i, kArrLcol, a.st);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Layout conversion: natural [B][n] rows <-> interleaved slabs.
 // ---------------------------------------------------------------------------
 struct InArgs {
@@ -1637,6 +1700,8 @@ struct mld_decoder {
     int schedule = MLD_SCHED_FLOODING;
     int check_rule = MLD_CHECK_SUM_PRODUCT;
     float ms_off_i = 0.f;  // min-sum offset, internal units
+    int checked = 0;       // validate the graph store before every decode
+    int32_t *status_host = nullptr;  // page-locked copy of the status word
     // early termination run by the device: capture stream, iteration counter
     // and cap (device), and the loop graphs built so far (per batch size,
     // variant and layering of the graph)
