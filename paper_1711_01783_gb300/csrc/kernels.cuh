@@ -672,6 +672,33 @@ void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cuda
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled before its predecessor on
+// the stream has finished; it waits here until that predecessor has
+// completed and its memory is visible, then lets its own successor be
+// scheduled.  Without the attribute both instructions return at once.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// ---------------------------------------------------------------------------
 // Layered schedule: the checks are updated one layer at a time, every check
 // from the latest messages.  The checks of a layer share no core VN, so a
 // check owns the posteriors of its core VNs while its layer runs: it forms
@@ -799,6 +826,7 @@ template <typename MsgT, int W, int DC, int DD>
 __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? kLayeredBlocksPerSm : 6))
     k_check_layered(CnArgs a, ClassLaunch cl, const int32_t *pos) {
     constexpr int TPC = W / kK;
+    pdl_enter();  // the previous layer's messages and posteriors
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -894,6 +922,7 @@ __device__ __forceinline__ void check_layered_irregular(const CnArgs &a, int32_t
 template <typename MsgT, int W>
 __global__ void __launch_bounds__(kBlock) k_check_layered_irregular(CnArgs a, ClassLaunch cl, const int32_t *pos) {
     constexpr int TPC = W / kK;
+    pdl_enter();
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -911,9 +940,9 @@ void launch_layered(const CnArgs &ca, const ClassLaunch &cl, const int32_t *pos,
     if constexpr (kAccWidth<MsgT, W>) {
         const dim3 grid(cl.blocks, slabs);
         const int dd = cl.deg - cl.dc;
-#define MLD_LCASE(DCV, DDV)                                                        \
-    case (DCV) * 2 + (DDV):                                                        \
-        k_check_layered<MsgT, W, DCV, DDV><<<grid, kBlock, 0, st>>>(ca, cl, pos); \
+#define MLD_LCASE(DCV, DDV)                                                                    \
+    case (DCV) * 2 + (DDV):                                                                    \
+        launch_pdl(k_check_layered<MsgT, W, DCV, DDV>, grid, dim3(kBlock), st, ca, cl, pos);  \
         return;
         if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
             switch (cl.dc * 2 + dd) {
@@ -925,7 +954,7 @@ void launch_layered(const CnArgs &ca, const ClassLaunch &cl, const int32_t *pos,
             }
         }
 #undef MLD_LCASE
-        k_check_layered_irregular<MsgT, W><<<grid, kBlock, 0, st>>>(ca, cl, pos);
+        launch_pdl(k_check_layered_irregular<MsgT, W>, grid, dim3(kBlock), st, ca, cl, pos);
     }
 }
 
