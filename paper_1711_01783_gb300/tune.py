@@ -1,4 +1,4 @@
-"""Slab-width autotuner for the decoder.
+"""Autotuner for the decoder: slab width and variable-update variant.
 
 The slab width W (codewords interleaved per 128-byte line group: 8, 16, 32
 or 64) trades padding against access granularity: a batch of 11 codewords
@@ -7,6 +7,12 @@ move whole 128-byte lines per graph access.  The tuner times a few decoder
 iterations for every width on the actual graph and batch size, keeps the
 fastest per decoded codeword, and caches the choice in a JSON file keyed by
 (graph signature, batch, message type, GPU name).
+
+``DecoderTuner`` widens the search for single-graph decoding without early
+termination to the variable-update variant as well: the gather pass or the
+accumulation of the new messages inside the check update (which wins with
+float messages and loses with half ones on GB300), over the slab widths each
+variant allows.  Plans keep the gather, so they use ``SlabWidthTuner``.
 """
 from __future__ import annotations
 
@@ -62,3 +68,53 @@ class SlabWidthTuner:
             with open(self.cache_path, "w") as f:
                 json.dump(self.cache, f, indent=1, sort_keys=True)
         return best
+
+
+class DecoderTuner(SlabWidthTuner):
+    """Chooses decoder options (slab width, variable-update variant) by
+    timing a few fixed iterations of each candidate on the actual graph and
+    batch; cached like the slab width."""
+
+    def _key(self, graph, batch: int, msg_dtype: str) -> str:
+        return "dec|" + super()._key(graph, batch, msg_dtype)
+
+    def candidates(self, msg_dtype: str):
+        default_w = 64 if msg_dtype == "f16" else 32
+        out = [dict(slab_width=w, vn_update="gather") for w in WIDTHS]
+        out.append(dict(slab_width=default_w, vn_update="accumulate"))
+        return out
+
+    def choose_options(self, graph, batch: int, msg_dtype: str = "f16") -> dict:
+        import torch
+
+        from . import Decoder, MldError
+        key = self._key(graph, batch, msg_dtype)
+        if key in self.cache:
+            return dict(self.cache[key]["opts"])
+        dev = torch.device("cuda", torch.cuda.current_device())
+        llr = torch.zeros((batch, graph.n_vn), dtype=torch.float32, device=dev)
+        syn = torch.zeros((batch, graph.n_cn), dtype=torch.uint8, device=dev)
+        times = []
+        for opts in self.candidates(msg_dtype):
+            try:
+                dec = Decoder(graph, batch, msg_dtype=msg_dtype, **opts)
+            except MldError:  # a variant the graph does not allow
+                continue
+            dec.decode(llr, syn, self.iters)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(self.reps):
+                dec.decode(llr, syn, self.iters)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append((e0.elapsed_time(e1) / self.reps, opts))
+            dec.close()
+        best = min(times, key=lambda t: t[0])[1]
+        self.cache[key] = {"opts": best, "ms": [[t, o] for t, o in times]}
+        self.trials[key] = times
+        if self.cache_path:
+            os.makedirs(os.path.dirname(os.path.abspath(self.cache_path)), exist_ok=True)
+            with open(self.cache_path, "w") as f:
+                json.dump(self.cache, f, indent=1, sort_keys=True)
+        return dict(best)

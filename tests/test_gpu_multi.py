@@ -92,3 +92,23 @@ def test_plan_rejects_bad_jobs(mld):
                    syndrome=torch.zeros((50, jobs[0]["g"].n_cn), dtype=torch.uint8, device="cuda"),
                    sigma=torch.ones(50, device="cuda"))
         mld.Plan([big])
+
+
+def test_decoder_tuner_picks_a_valid_fastest_option(mld, tmp_path):
+    from paper_1711_01783_gb300.tune import DecoderTuner
+    g0 = preset_graph(0.1, 4096, 1)
+    g = mld.Graph.from_edges(g0)
+    tuner = DecoderTuner(str(tmp_path / "tune.json"), iters=3, reps=2)
+    for msg in ("f16", "f32"):
+        opts = tuner.choose_options(g, 64, msg)
+        times = tuner.trials[tuner._key(g, 64, msg)]
+        assert opts == min(times, key=lambda t: t[0])[1]
+        assert len(times) == 5                       # 4 widths with the gather + accumulation
+        dec = mld.Decoder(g, 64, msg_dtype=msg, **opts)   # the choice builds a working decoder
+        w = make_workload(0.1, 4096, 64, 1, 9300, beta=0.35, graph=g0)
+        out = dec.decode_y(_dev(w.y), _dev(w.sigma), _dev(w.s), 20)
+        assert out["bits"].shape == (64, 4096)
+    # cached: a new tuner reads the same choice without timing
+    again = DecoderTuner(str(tmp_path / "tune.json"))
+    assert again.choose_options(g, 64, "f16") == tuner.choose_options(g, 64, "f16")
+    assert not again.trials
