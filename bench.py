@@ -256,7 +256,8 @@ def measured_peak_hbm() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def run_uneven(a, world, rank, local):
+def uneven_record(total: int, beta: float, msg: str, steps: int, warmup: int, rank: int, dev,
+                  tune_cache=None) -> dict:
     """Uneven batch: every codeword draws its (rate, length); one plan (one
     CUDA-graph launch) decodes all groups with per-codeword early termination
     and each rate's iteration cap; slab widths chosen by the autotuner."""
@@ -265,51 +266,62 @@ def run_uneven(a, world, rank, local):
     from paper_1711_01783_gb300.tune import SlabWidthTuner
     from synthetic import make_uneven_workload
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    groups = make_uneven_workload(a.batch, seed=3 + rank, beta=a.beta)
-    tuner = SlabWidthTuner(a.tune_cache)
+    groups = make_uneven_workload(total, seed=3 + rank, beta=beta)
+    tuner = SlabWidthTuner(tune_cache)
     jobs, widths = [], {}
     for rate, n, wl in groups:
         g = mld.Graph.from_edges(wl.graph)
         B = wl.y.shape[0]
-        W = tuner.choose(g, B, a.msg)
+        W = tuner.choose(g, B, msg)
         widths[f"{rate}/{n}"] = (B, W)
-        jobs.append(dict(decoder=mld.Decoder(g, B, msg_dtype=a.msg, slab_width=W), y=torch.from_numpy(wl.y).to(dev),
+        jobs.append(dict(decoder=mld.Decoder(g, B, msg_dtype=msg, slab_width=W), y=torch.from_numpy(wl.y).to(dev),
                          sigma=torch.from_numpy(wl.sigma).to(dev), syndrome=torch.from_numpy(wl.s).to(dev),
                          max_iters=DEFAULT_ITERS[rate]))
     plan = mld.Plan(jobs, early_term=True)
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         plan.launch()
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        outs = plan.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    bits = sum(wl.y.shape[0] * wl.y.shape[1] for _, _, wl in groups)
+    rec = {"value": bits / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+           "workload": f"{total} codewords, (rate, n) uniform over {{0.1,0.05,0.02}} x {{2^16,2^18,10^6}}, "
+                       f"caps 100/150/200, early termination, beta={beta}, {msg} messages",
+           "groups (batch, slab width)": widths, "gpu_launches": plan.launches * steps,
+           "frames_converged": sum(int(o["converged"].sum().item()) for o in outs),
+           "mean_iters": [round(float(o["iters_used"].float().mean().item()), 2) for o in outs]}
+    plan.close()
+    return rec
+
+
+def run_uneven(a, world, rank, local):
+    """The uneven batch as the workload of the line (--workload uneven)."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         uuid = None
     clocks = ClockSampler(uuid)
     clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(a.steps):
-        outs = plan.launch()
-    e1.record()
-    torch.cuda.synchronize()
+    rec = uneven_record(a.batch, a.beta, a.msg, a.steps, a.warmup, rank, dev, a.tune_cache)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / a.steps
-    bits = sum(wl.y.shape[0] * wl.y.shape[1] for _, _, wl in groups)
-    conv = sum(int(o["converged"].sum().item()) for o in outs)
-    its = [int(o["iters_used"].float().mean().item()) for o in outs]
     line = {
         "metric": "decoded Mbit/s, uneven batch (mixed rates and lengths, early termination)",
-        "value": bits / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MET ensembles, BIAWGN samples)",
-        "config": {"workload": f"{a.batch} codewords, (rate, n) uniform over {{0.1,0.05,0.02}} x "
-                               f"{{2^16,2^18,10^6}}, caps 100/150/200, early termination, beta={a.beta}",
-                   "msg_storage": a.msg, "groups (batch, slab width)": widths,
+        "config": {"workload": rec["workload"], "msg_storage": a.msg,
+                   "groups (batch, slab width)": rec["groups (batch, slab width)"],
                    "l2": "n=10^6 groups exceed L2"},
-        "gpu_launches": plan.launches * a.steps, "frames_converged": conv, "mean_iters": its,
-        "clocks": clk,
+        "gpu_launches": rec["gpu_launches"], "frames_converged": rec["frames_converged"],
+        "mean_iters": rec["mean_iters"], "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -785,6 +797,7 @@ def main():
         sub["rules_converging"] = rule_comparison(a, dev, barrier)
         sub["md_frontend"] = md_frontend(a, dev, peak)
         sub["peg"] = peg_record(dev)
+        sub["uneven"] = uneven_record(96, a.beta, a.msg, 3, 1, rank, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
