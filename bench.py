@@ -328,18 +328,20 @@ def run_uneven(a, world, rank, local):
 
 
 def run_wbp(a, world, rank, local):
-    """Weighted BP: train the per-(iteration, edge type) weights on decoder-
-    generated samples (rate 0.1, n = 10^5, 16 codewords, T = 20, checkpoint
-    every 5), then compare the frame error rate of the trained and the unit
-    weights (plain BP) at n = 10^6.  value = training throughput (codeword
-    bits through forward + adjoint per second)."""
+    """Weighted BP: for T = 10, 15 and 20 unrolled iterations, train the
+    per-(iteration, edge type) weights on decoder-generated samples (rate 0.1,
+    n = 10^5, 16 codewords, checkpoint every 5, Adam on the mean BCE), then
+    compare the frame error rate of the trained weights with unit weights
+    (plain BP) after the same T iterations at n = 10^6: an iterations-to-FER
+    curve.  value = training throughput at T = 20 (codeword bits through
+    forward + adjoint per second)."""
     import torch
     import paper_1711_01783_gb300 as mld
     from synthetic import make_workload, preset_graph
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n_tr, B_tr, T, k = 100_000, 16, 20, 5
+    n_tr, B_tr, k = 100_000, 16, 5
     beta = a.beta
     g_tr = preset_graph(0.1, n_tr, 10)
     G_tr = mld.Graph.from_edges(g_tr)
@@ -353,63 +355,63 @@ def run_wbp(a, world, rank, local):
 
     data = [batch(20_000 + i) for i in range(16)]
     val = batch(40_000)
-    wt = torch.ones((T, 3), device=dev, requires_grad=True)
-    opt = torch.optim.Adam([wt], lr=0.003)
-    losses = []
-
-    def val_loss():
-        with torch.no_grad():
-            soft, _ = dec.wbp_forward(val[0], val[1], wt.detach(), keep_tape=False)
-            return float(torch.nn.functional.softplus(-val[2] * soft).mean())
-
-    val_before = val_loss()
-
-    def step(i):
-        llr, s, y = data[i % len(data)]
-        opt.zero_grad()
-        soft = mld.weighted_bp(dec, llr, s, wt, ckpt_k=k)
-        loss = torch.nn.functional.softplus(-y * soft).mean()
-        loss.backward()
-        opt.step()
-        return loss
-
-    for i in range(a.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for i in range(a.train_steps):
-        losses.append(step(a.warmup + i))
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / a.train_steps
-    losses = [float(x.detach()) for x in losses]
-    val_after = val_loss()
-
-    # held-out evaluation: FER at n = 10^6 of unit weights (plain BP) and of the trained weights
+    # held-out evaluation set at n = 10^6
     n_ev, B_ev = 1_000_000, 64
-    wl = make_workload(0.1, n_ev, B_ev, 11, 30_000, beta=beta)
-    G_ev = mld.Graph.from_edges(wl.graph)
-    dec_ev = mld.Decoder(G_ev, B_ev, msg_dtype="f32")
-    llr = torch.from_numpy(2.0 * wl.y / (wl.sigma[:, None] ** 2)).to(dev)
-    s = torch.from_numpy(wl.s).to(dev)
-    x = torch.from_numpy(wl.x).to(dev)
-    fer = {}
-    for name, wv in (("plain", torch.ones((T, 3), device=dev)), ("weighted", wt.detach())):
-        soft, _ = dec_ev.wbp_forward(llr, s, wv, keep_tape=False)
-        bits = (soft < 0).to(torch.uint8)
-        fer[name] = float((bits != x).any(dim=1).float().mean())
+    wl_ev = make_workload(0.1, n_ev, B_ev, 11, 30_000, beta=beta)
+    dec_ev = mld.Decoder(mld.Graph.from_edges(wl_ev.graph), B_ev, msg_dtype="f32")
+    llr_ev = torch.from_numpy(2.0 * wl_ev.y / (wl_ev.sigma[:, None] ** 2)).to(dev)
+    s_ev = torch.from_numpy(wl_ev.s).to(dev)
+    x_ev = torch.from_numpy(wl_ev.x).to(dev)
+
+    curve = {}
+    ms = None
+    for T in (10, 15, 20):
+        wt = torch.ones((T, 3), device=dev, requires_grad=True)
+        opt = torch.optim.Adam([wt], lr=0.003)
+
+        def val_loss():
+            with torch.no_grad():
+                soft, _ = dec.wbp_forward(val[0], val[1], wt.detach(), keep_tape=False)
+                return float(torch.nn.functional.softplus(-val[2] * soft).mean())
+
+        def step(i):
+            llr, s, y = data[i % len(data)]
+            opt.zero_grad()
+            soft = mld.weighted_bp(dec, llr, s, wt, ckpt_k=k)
+            loss = torch.nn.functional.softplus(-y * soft).mean()
+            loss.backward()
+            opt.step()
+            return loss
+
+        before = val_loss()
+        for i in range(a.warmup):
+            step(i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(a.train_steps):
+            step(a.warmup + i)
+        e1.record()
+        torch.cuda.synchronize()
+        if T == 20:
+            ms = e0.elapsed_time(e1) / a.train_steps
+        after = val_loss()
+        rec = {"val_loss_unit_weights": before, "val_loss_trained": after,
+               "weights_mean_per_type": wt.detach().mean(dim=0).tolist()}
+        for name, wv in (("plain", torch.ones((T, 3), device=dev)), ("weighted", wt.detach())):
+            soft, _ = dec_ev.wbp_forward(llr_ev, s_ev, wv, keep_tape=False)
+            bits = (soft < 0).to(torch.uint8)
+            rec[f"fer_{name}"] = float((bits != x_ev).any(dim=1).float().mean())
+            rec[f"ber_{name}"] = float((bits != x_ev).float().mean())
+        curve[f"T{T}"] = rec
     line = {
         "metric": "weighted-BP training throughput (forward + adjoint), codeword bits per second",
         "value": B_tr * n_tr / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world, "steps": a.train_steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MET ensemble, BIAWGN samples)",
-        "config": {"workload": f"rate 0.1, n={n_tr}, {B_tr} codewords, T={T}, checkpoint every {k}, "
-                               f"20x3 weights, Adam lr 0.003, beta={beta}; evaluated at n={n_ev}, {B_ev} codewords"},
-        "val_loss_unit_weights": val_before, "val_loss_trained": val_after,
-        "train_loss_first5": float(np.mean(losses[:5])), "train_loss_last5": float(np.mean(losses[-5:])),
-        "fer_plain_T20": fer["plain"], "fer_weighted_T20": fer["weighted"],
-        "weights_mean_per_type": wt.detach().mean(dim=0).tolist(),
+        "config": {"workload": f"rate 0.1, n={n_tr}, {B_tr} codewords, T=10/15/20, checkpoint every {k}, "
+                               f"Tx3 weights, Adam lr 0.003, beta={beta}; evaluated at n={n_ev}, {B_ev} codewords"},
+        "iterations_to_fer": curve,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
