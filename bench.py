@@ -456,17 +456,20 @@ def kernel_summary(kt: dict, st: dict, msg: str, batch: int, iters: int, steps: 
 
 
 def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: float,
-               vn_update: str = "gather", schedule: str = "flooding", check_rule: str = "sum_product") -> dict:
+               vn_update: str = "gather", schedule: str = "flooding", check_rule: str = "sum_product",
+               structured: bool = False) -> dict:
     """One more fixed-iteration workload measured like the headline (device-
-    resident inputs, CUDA events, max over ranks), with fewer steps."""
+    resident inputs, CUDA events, max over ranks), with fewer steps.
+    structured: the layer-structured ensemble, decoded with its own layers."""
     import torch
     import paper_1711_01783_gb300 as mld
-    from synthetic import make_workload
+    from synthetic import make_workload, preset_graph_layered
     iters = DEFAULT_ITERS[rate]
-    wl = make_workload(rate, a.n, a.batch, 2, rank_data_seed(rank), beta=a.beta)
+    graph = preset_graph_layered(rate, a.n, 2) if structured else None
+    wl = make_workload(rate, a.n, a.batch, 2, rank_data_seed(rank), beta=a.beta, graph=graph)
     g = mld.Graph.from_edges(wl.graph)
     if schedule == "layered":
-        g.set_layers(None)
+        g.set_layers(wl.graph.meta["layer_of_check"] if structured else None)
     dec = mld.Decoder(g, a.batch, msg_dtype=msg, vn_update=vn_update, schedule=schedule, check_rule=check_rule)
     y = torch.from_numpy(wl.y).to(dev)
     sig = torch.from_numpy(wl.sigma).to(dev)
@@ -492,7 +495,8 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     rec = {"value": job_throughput(world, a.batch, a.n, a.sub_steps, ms_max), "unit": UNIT,
            "ms_per_step": ms_max / a.sub_steps, "steps": a.sub_steps, "warmup": 3,
            "rate": rate, "iters": iters, "msg_storage": msg, "vn_update": vn_update, "schedule": schedule,
-           "check_rule": check_rule,
+           "check_rule": check_rule, "ensemble": "layer-structured" if structured else "plain",
+           "n_layers": g.layers()[1] if schedule == "layered" else None,
            "gpu_launches": launches,
            "frames_converged": conv, "fer": 1.0 - conv / a.batch}
     rec.update({k: ks[k] for k in ("frac", "frac_decode", "pass_ms", "var_update_ms", "share_check")})
@@ -607,20 +611,24 @@ def rule_comparison(a, dev, barrier, beta: float = 0.30, cap: int = 100, steps: 
     return res
 
 
-def schedule_comparison(a, dev, barrier, betas=(0.40, 0.42), cap: int = 100, steps: int = 5) -> dict:
+def schedule_comparison(a, dev, barrier, betas=(0.40, 0.42), cap: int = 100, steps: int = 5,
+                        structured: bool = False) -> dict:
     """Flooding against the layered schedule where frames converge: rate 0.1,
     n = 10^6, 64 codewords, early termination with a cap of 100 iterations.
-    Per (beta, schedule): decode time, decoded Mbit/s, mean iterations, FER."""
+    Per (beta, schedule): decode time, decoded Mbit/s, mean iterations, FER.
+    structured: the layer-structured ensemble, layered with its own groups."""
     import torch
     import paper_1711_01783_gb300 as mld
-    from synthetic import make_workload, preset_graph
-    graph = preset_graph(0.1, a.n, 2)
+    from synthetic import make_workload, preset_graph, preset_graph_layered
+    graph = preset_graph_layered(0.1, a.n, 2) if structured else preset_graph(0.1, a.n, 2)
     g = mld.Graph.from_edges(graph)
-    g.set_layers(None)
+    g.set_layers(graph.meta["layer_of_check"] if structured else None)
     n_layers = g.layers()[1]
     stream = torch.cuda.current_stream()
+    how = "the ensemble's own check groups" if structured else "the library's default layering"
     res = {"workload": f"rate 0.1, n={a.n}, {a.batch} codewords, early termination, cap {cap}, "
-                       f"{a.msg} messages; layered: the library's default layering ({n_layers} layers)"}
+                       f"{a.msg} messages, {'layer-structured' if structured else 'plain'} ensemble; "
+                       f"layered: {how} ({n_layers} layers)"}
     for beta in betas:
         wl = make_workload(0.1, a.n, a.batch, 2, 7000, beta=beta, graph=graph)
         y = torch.from_numpy(wl.y).to(dev)
@@ -794,6 +802,10 @@ def main():
         sub[f"rate{a.rate}_{a.msg}_layered"] = sub_record(a.rate, a.msg, a, rank, dev, dist, barrier, peak,
                                                           "gather", "layered")
         sub["schedules_converging"] = schedule_comparison(a, dev, barrier)
+        sub[f"rate{a.rate}_{a.msg}_layered_structured"] = sub_record(a.rate, a.msg, a, rank, dev, dist, barrier,
+                                                                     peak, "gather", "layered", structured=True)
+        sub["schedules_converging_structured"] = schedule_comparison(a, dev, barrier, betas=(0.40, 0.42),
+                                                                     structured=True)
         sub[f"rate{a.rate}_{a.msg}_minsum"] = sub_record(a.rate, a.msg, a, rank, dev, dist, barrier, peak,
                                                          check_rule="min_sum")
         sub["rules_converging"] = rule_comparison(a, dev, barrier)

@@ -16,14 +16,15 @@ the workload the decoder is given.
   that share no VN of degree >= 2, which fixes the check order of the layered
   (serial) schedule.
 """
-from .ensemble import MetGraph, met_ensemble, RATE_PRESETS, preset_graph
+from .ensemble import (MetGraph, met_ensemble, RATE_PRESETS, preset_graph, met_ensemble_layered,
+                       preset_graph_layered)
 from .channel import (biawgn_capacity, awgn_capacity, sigma_for_beta,
                       random_bits, bob_syndrome, biawgn_observe, Workload,
                       make_workload, make_uneven_workload)
 from .layers import check_layers, layer_order
 
 __all__ = [
-    "MetGraph", "met_ensemble", "RATE_PRESETS", "preset_graph",
+    "MetGraph", "met_ensemble", "RATE_PRESETS", "preset_graph", "met_ensemble_layered", "preset_graph_layered",
     "biawgn_capacity", "awgn_capacity", "sigma_for_beta", "random_bits",
     "bob_syndrome", "biawgn_observe", "Workload", "make_workload", "make_uneven_workload",
     "check_layers", "layer_order",

@@ -143,6 +143,83 @@ def met_ensemble(n: int, rate: float, core_frac: float, d2: int, seed: int,
                     meta=dict(core_frac=core_frac, frac_two=frac_two))
 
 
+def _split(total: int, weights) -> np.ndarray:
+    """Integers proportional to weights summing to total (largest remainder),
+    each at least 1."""
+    w = np.asarray(weights, dtype=np.float64)
+    raw = total * w / w.sum()
+    out = np.maximum(np.floor(raw).astype(np.int64), 1)
+    rest = total - out.sum()
+    order = np.argsort(-(raw - np.floor(raw)), kind="stable")
+    for i in range(int(rest)):
+        out[order[i % len(out)]] += 1
+    return out
+
+
+def met_ensemble_layered(n: int, rate: float, core_frac: float, d2: int, seed: int,
+                         frac_two: float = 0.4) -> MetGraph:
+    """The same family with layer structure, as codes meant for layered
+    decoding are built: the type-2 checks form d2 groups of equal size and
+    the k-th type-2 edge of every core VN goes to group k; the type-1 checks
+    form three groups (sized in proportion to their edges) and the j-th
+    type-1 edge of a core VN goes to group j.  Inside a group the sockets are
+    dealt evenly and shuffled as in met_ensemble, so the degree distribution
+    is the same; a group holds at most one edge of each core VN, so it is a
+    layer (no repeated pairs arise either).  meta["layer_of_check"] gives
+    each check's group: the type-2 groups are layers 0 .. d2-1, the type-1
+    groups layers d2 .. d2+2."""
+    n_c = int(round(core_frac * n))
+    m2 = n - n_c
+    m1 = n_c - int(round(rate * n))
+    if n_c < 1 or m1 < 3 or m2 < d2 or d2 < 1:
+        raise ValueError(f"degenerate ensemble n={n} rate={rate} core_frac={core_frac}")
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(n), int(d2), 2]))
+    n_two = int(round(frac_two * n_c))
+    members1 = [np.arange(n_c), np.arange(n_c), np.arange(n_two, n_c)]
+    sizes1 = _split(m1, [len(mb) for mb in members1])
+    sizes2 = _split(m2, np.ones(d2))
+    evs, ecs, ets = [], [], []
+    layer = np.zeros(m1 + m2, dtype=np.int32)
+    base = 0
+    for j, vs in enumerate(members1):
+        evs.append(vs)
+        ecs.append(base + rng.permutation(_deal(vs.shape[0], int(sizes1[j]))))
+        ets.append(np.full(vs.shape[0], EDGE_T1, np.uint8))
+        layer[base:base + sizes1[j]] = d2 + j
+        base += int(sizes1[j])
+    for k in range(d2):
+        vs = np.arange(n_c)
+        evs.append(vs)
+        ecs.append(base + rng.permutation(_deal(n_c, int(sizes2[k]))))
+        ets.append(np.full(n_c, EDGE_T2, np.uint8))
+        layer[base:base + sizes2[k]] = k
+        base += int(sizes2[k])
+    # degree-1 VN n_c + j <-> type-2 check m1 + j
+    evs.append(n_c + np.arange(m2))
+    ecs.append(m1 + np.arange(m2))
+    ets.append(np.full(m2, EDGE_T2_DEG1, np.uint8))
+    ev, ec, et = np.concatenate(evs), np.concatenate(ecs), np.concatenate(ets)
+    m = m1 + m2
+    vlab = rng.permutation(n)
+    clab = rng.permutation(m)
+    ev, ec = vlab[ev], clab[ec]
+    lay = np.zeros(m, dtype=np.int32)
+    lay[clab] = layer
+    order = np.lexsort((ev, ec))
+    return MetGraph(n_vn=n, n_cn=m,
+                    edge_vn=np.ascontiguousarray(ev[order], dtype=np.int32),
+                    edge_cn=np.ascontiguousarray(ec[order], dtype=np.int32),
+                    edge_type=np.ascontiguousarray(et[order]),
+                    rate=rate, n_core=n_c, m1=m1, m2=m2, d2=d2, seed=seed,
+                    meta=dict(core_frac=core_frac, frac_two=frac_two, layer_of_check=lay, n_layers=d2 + 3))
+
+
+def preset_graph_layered(rate: float, n: int, seed: int) -> MetGraph:
+    """The layer-structured ensemble for one of the three code rates."""
+    p = RATE_PRESETS[rate]
+    return met_ensemble_layered(n, rate, p["core_frac"], p["d2"], seed)
+
+
 def preset_graph(rate: float, n: int, seed: int) -> MetGraph:
     """The ensemble for one of the three code rates (0.1, 0.05, 0.02)."""
     p = RATE_PRESETS[rate]

@@ -83,3 +83,30 @@ def test_syndrome_and_observation_shapes_and_seeding():
     w2 = make_workload(0.1, 4096, 2, 1, 1000, graph=g)
     assert np.array_equal(w2.x, w.x[:2]) and np.array_equal(w2.y, w.y[:2])
     assert w.y.dtype == np.float32 and abs(np.std(w.y + (2.0 * w.x - 1)) - w.sigma[0]) < 0.05
+
+
+@pytest.mark.parametrize("rate", [0.1, 0.05, 0.02])
+def test_layer_structured_ensemble(rate):
+    """Same degree structure as the plain ensemble; its check groups are
+    VN-disjoint layers, d2 + 3 of them."""
+    from synthetic import preset_graph_layered
+    n = 20000
+    g = preset_graph_layered(rate, n, 5)
+    ref = preset_graph(rate, n, 5)
+    assert (g.n_vn, g.n_cn, g.n_edges, g.m1, g.m2) == (ref.n_vn, ref.n_cn, ref.n_edges, ref.m1, ref.m2)
+    np.testing.assert_array_equal(np.bincount(g.vn_degree()), np.bincount(ref.vn_degree()))
+    for t in (EDGE_T1, EDGE_T2, EDGE_T2_DEG1):
+        assert (g.edge_type == t).sum() == (ref.edge_type == t).sum()
+    key = g.edge_vn.astype(np.int64) * g.n_cn + g.edge_cn
+    assert np.unique(key).size == key.size
+    lay = g.meta["layer_of_check"]
+    assert lay.shape == (g.n_cn,) and g.meta["n_layers"] == RATE_PRESETS[rate]["d2"] + 3
+    assert np.array_equal(np.unique(lay), np.arange(g.meta["n_layers"]))
+    core = g.vn_degree()[g.edge_vn] > 1
+    pair = lay[g.edge_cn[core]].astype(np.int64) * g.n_vn + g.edge_vn[core]
+    assert np.unique(pair).size == pair.size       # no core VN twice in a layer
+    # check degrees within one type differ by at most one
+    for t in (EDGE_T1, EDGE_T2):
+        cd = np.bincount(g.edge_cn[g.edge_type == t], minlength=g.n_cn)
+        cd = cd[cd > 0]
+        assert cd.max() - cd.min() <= 1
