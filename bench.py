@@ -84,7 +84,7 @@ TIMING_EVERY = 10
 CHECK_PASS_TRAFFIC_PER_CW_BIT = {(0.1, "f16"): 396.62e6 / (64 * 3e5)}
 
 
-def algorithmic_bytes(st: dict, msg: str) -> tuple[float, float]:
+def algorithmic_bytes(st: dict, msg: str, schedule: str = "flooding") -> tuple[float, float]:
     """Minimum bytes per codeword of one check-update pass and of one whole
     iteration, at message width b (2 for half storage, 4 for float):
       check pass: r read and written on every core edge (2 b e_core), the
@@ -92,9 +92,17 @@ def algorithmic_bytes(st: dict, msg: str) -> tuple[float, float]:
         (4 n_core), syndrome bits (m / 8);
       iteration: r read and written once (2 b e_core), degree-1 terms
         (b m2), core VNs: channel term read, posterior written and read
-        (n_core (b + 8)), syndrome bits (m / 8)."""
+        (n_core (b + 8)), syndrome bits (m / 8).
+    Layered schedule (the pass is the whole iteration): r read and written
+    once (2 b e_core); a core VN's posterior is read and written in every
+    layer that holds one of its checks, once per core edge (8 e_core: the
+    posteriors, 4 B per codeword and VN, exceed L2 at full size); degree-1
+    terms (b m2); syndrome bits (m / 8)."""
     b = 2 if msg == "f16" else 4
     e, m2, nc, m = st["e_core"], st["n_deg1"], st["n_core"], st["n_cn"]
+    if schedule == "layered":
+        it = 2 * b * e + 8 * e + b * m2 + m / 8
+        return it, it
     check = 2 * b * e + b * m2 + 4 * nc + m / 8
     iteration = 2 * b * e + b * m2 + nc * (b + 8) + m / 8
     return check, iteration
@@ -438,10 +446,11 @@ def time_steps(step, steps: int, warmup: int, stream, barrier) -> float:
 
 
 def kernel_summary(kt: dict, st: dict, msg: str, batch: int, iters: int, steps: int, ms_step: float,
-                   peak: float) -> dict:
+                   peak: float, schedule: str = "flooding") -> dict:
     """Check-pass and whole-decode roofline fractions from the library's
-    per-iteration CUDA events (one timed region = one pass)."""
-    check_b, iter_b = algorithmic_bytes(st, msg)
+    per-iteration CUDA events (one timed region = one pass; with the layered
+    schedule the pass is the iteration's layers)."""
+    check_b, iter_b = algorithmic_bytes(st, msg, schedule)
     check_ms = kt["check_ms"] / max(1, kt["check_timed"])
     var_ms = kt["var_ms"] / max(1, kt["var_timed"])
     achieved = check_b * batch / (check_ms * 1e-3) / 1e9
@@ -490,7 +499,7 @@ def sub_record(rate: float, msg: str, a, rank: int, dev, dist, barrier, peak: fl
     ms_max, launches = reduce_over_ranks(dist, ms, kt["check_launches"] + kt["var_launches"]
                                          + kt["syndrome_launches"] + kt["layout_launches"], dev)
     world = dist.get_world_size() if dist is not None else 1
-    ks = kernel_summary(kt, g.stats, msg, a.batch, iters, a.sub_steps, ms_max / a.sub_steps, peak)
+    ks = kernel_summary(kt, g.stats, msg, a.batch, iters, a.sub_steps, ms_max / a.sub_steps, peak, schedule)
     conv = int(out["converged"].sum().item())
     rec = {"value": job_throughput(world, a.batch, a.n, a.sub_steps, ms_max), "unit": UNIT,
            "ms_per_step": ms_max / a.sub_steps, "steps": a.sub_steps, "warmup": 3,

@@ -39,3 +39,16 @@ def test_iteration_bytes_match_the_scope_table(rate, msg):
 def test_check_pass_bytes_of_the_headline():
     check, _ = bench.algorithmic_bytes(_stats(0.1), "f16")
     assert check / 1e6 == pytest.approx(20.59, abs=0.006)   # 1.318 GB per pass at 64 codewords
+
+
+def test_layered_iteration_bytes():
+    """Layered: per core edge r in and out plus the VN's posterior read and
+    written in that edge's layer (2 b + 8 bytes); at rate 0.1, n = 10^6,
+    half messages: 4.52e6 x 12 + 2 x 8e5 + 9e5 / 8 = 55.95 MB."""
+    st = _stats(0.1)
+    assert st["e_core"] == 4_520_000
+    check, iteration = bench.algorithmic_bytes(st, "f16", "layered")
+    assert check == iteration
+    assert iteration / 1e6 == pytest.approx(55.95, abs=0.006)
+    _, it32 = bench.algorithmic_bytes(st, "f32", "layered")
+    assert it32 - iteration == pytest.approx(4 * st["e_core"] + 2 * st["n_deg1"])

@@ -199,13 +199,16 @@ def test_irregular_graph_against_the_layered_oracle(mld):
 
 
 @pytest.mark.parametrize("n,B,beta,iters,sample", [
-    (4096, 16, 0.40, 60, None),
+    (4096, 16, 0.30, 60, None),
     (1_000_000, 64, 0.40, 100, [0, 37, 63]),
 ])
 def test_layer_structured_ensemble(mld, n, B, beta, iters, sample):
     """The layer-structured ensemble decoded with its own check groups as
     layers (d2 + 3 = 23 at rate 0.1): against the layered oracle in the same
-    order, float and half messages, early termination."""
+    order, float and half messages, early termination.  The short code runs
+    at beta = 0.30: at 0.40 it sits at its finite-length threshold (about
+    half the frames fail), where half-precision rounding moves the iteration
+    at which single frames converge by tens of iterations."""
     from synthetic import preset_graph_layered
     g0 = preset_graph_layered(0.1, n, 4)
     lay = g0.meta["layer_of_check"]
@@ -222,7 +225,7 @@ def test_layer_structured_ensemble(mld, n, B, beta, iters, sample):
         conv = _np(out["converged"]).astype(bool)
         assert np.array_equal(_syndrome_holds(g0, _np(out["bits"]), w.s), conv)
         sub = {k: (v[sel] if v is not None else None) for k, v in out.items()}
-        _check_frames(sub, ref, g0, w.s[sel], msg, near_threshold=True)
+        _check_frames(sub, ref, g0, w.s[sel], msg, near_threshold=msg == "f16")
         print(f"n={n} {msg}: structured layered converged {conv.sum()}/{B}, mean iterations "
               f"{_np(out['iters_used']).mean():.2f} (oracle {ref['iters_used'].mean():.2f})")
         dec.close()
