@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--vn-update", default="gather", choices=["gather", "accumulate"],
                     help="variable update of the headline decoder: CSC gather (deterministic) or "
                          "accumulation of the new messages inside the check update (atomic adds)")
+    ap.add_argument("--staging", default="direct", choices=["direct", "bulk", "bulk_lsu"],
+                    help="check-update operands of the headline decoder: read directly, or staged in "
+                         "shared memory by bulk copies one group of checks ahead")
     return ap.parse_args()
 
 
@@ -113,7 +116,7 @@ def workload_config(a) -> dict:
         "workload": (f"synthetic MET-LDPC rate {a.rate}, n={a.n}, {a.batch} codewords, "
                      f"{a.iters} fixed BP iterations, beta={a.beta}"),
         "rate": a.rate, "n": a.n, "codewords": a.batch, "iters": a.iters,
-        "beta": a.beta, "msg_storage": a.msg, "vn_update": a.vn_update,
+        "beta": a.beta, "msg_storage": a.msg, "vn_update": a.vn_update, "staging": a.staging,
         "l2": "inputs and message state larger than L2 (no flush needed)",
         "parallelism": "replicas",
     }
@@ -712,7 +715,7 @@ def main():
 
     wl = make_workload(a.rate, a.n, a.batch, seed_graph, rank_data_seed(rank), beta=a.beta)
     g = mld.Graph.from_edges(wl.graph)
-    dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, slab_width=a.slab, vn_update=a.vn_update)
+    dec = mld.Decoder(g, a.batch, msg_dtype=a.msg, slab_width=a.slab, vn_update=a.vn_update, staging=a.staging)
     st = g.stats
     y = torch.from_numpy(wl.y).to(dev)
     sig = torch.from_numpy(wl.sigma).to(dev)

@@ -46,9 +46,8 @@ extern "C" {
 #define MLD_EINVAL   (-1)  /* bad argument (null pointer, size, flag, dtype)   */
 #define MLD_ENOMEM   (-2)  /* host or device allocation failed                  */
 #define MLD_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed        */
-#define MLD_ETIMEOUT (-4)  /* reserved for a bounded device-side wait that gives
-                              up; no entry point waits on the device, so none
-                              returns it                                      */
+#define MLD_ETIMEOUT (-4)  /* a bounded device-side wait gave up (reported by
+                              mld_decode_status; see mld_opts.staging)        */
 #define MLD_EGRAPH   (-5)  /* malformed Tanner graph (index out of range, ...)   */
 
 /* ---- edge-message storage type (mld_opts.msg_dtype) ---------------------- */
@@ -253,6 +252,21 @@ int mld_peg_edges(int32_t n_vn, int32_t n_types, const int32_t *deg, int32_t n_c
  *                The result is kept for mld_decode_status.  A debugging aid
  *                for programs that may write stray device memory; plans do
  *                not check.
+ *   staging    : MLD_STAGE_DIRECT (default): the check update reads its
+ *                operands from device memory as it goes.  MLD_STAGE_BULK:
+ *                where it applies (half messages at slab width 64,
+ *                sum-product, flooding, MLD_VN_GATHER, checks of at most six
+ *                terms with at most one degree-1 VN, and not the
+ *                decisions-only early-termination pass), the operands of
+ *                each group of 8 checks are brought into shared memory by
+ *                bulk copies one group ahead of the arithmetic, one copy per
+ *                posterior row; MLD_STAGE_BULK_LSU: the same, with the
+ *                posterior rows copied 16 bytes per thread by cp.async.
+ *                Results are bit-identical to MLD_STAGE_DIRECT (and slower
+ *                on GB300: the direct kernel is instruction-bound).  Waits
+ *                are bounded (2 s): a copy that never completes makes the
+ *                decode's results invalid and mld_decode_status return
+ *                MLD_ETIMEOUT.
  * Errors: MLD_EINVAL, MLD_ENOMEM, MLD_ECUDA. */
 #define MLD_VN_GATHER         0
 #define MLD_VN_ACCUMULATE     1
@@ -260,6 +274,9 @@ int mld_peg_edges(int32_t n_vn, int32_t n_types, const int32_t *deg, int32_t n_c
 #define MLD_SCHED_LAYERED     1
 #define MLD_CHECK_SUM_PRODUCT 0
 #define MLD_CHECK_MIN_SUM     1
+#define MLD_STAGE_DIRECT      0
+#define MLD_STAGE_BULK        1
+#define MLD_STAGE_BULK_LSU    2
 typedef struct {
     int32_t msg_dtype;
     int32_t max_batch;
@@ -270,7 +287,8 @@ typedef struct {
     int32_t check_rule;
     float ms_offset;
     int32_t checked;
-    int32_t reserved[7];  /* must be zero */
+    int32_t staging;
+    int32_t reserved[6];  /* must be zero */
 } mld_opts;
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out);
 int mld_decoder_destroy(mld_decoder *d);
@@ -317,11 +335,13 @@ int mld_decode_y(mld_decoder *d, const float *y, const float *sigma,
                  uint32_t flags, uint8_t *bits_out, float *post_out,
                  uint8_t *converged, int32_t *iters_used, void *stream);
 
-/* Status of the device-side check of the last decode call of a decoder
- * created with `checked` (MLD_OK if the graph store was intact, or for other
- * decoders); on a corrupted store, MLD_EGRAPH with the array, index and value
- * in mld_last_error().  Reads the decoder's device status word with a
- * blocking copy; call after the stream is idle. */
+/* Status of the decoder's device-side checks: MLD_OK, or MLD_EGRAPH when
+ * the check of a decoder created with `checked` found the graph store
+ * corrupted in its last decode call (array, index and value in
+ * mld_last_error()), or MLD_ETIMEOUT when a staged check update
+ * (MLD_STAGE_BULK) gave up waiting for a copy in some earlier call (sticky:
+ * that decoder's later results are not to be trusted).  Reads the device
+ * status word with a blocking copy; call after the stream is idle. */
 int mld_decode_status(mld_decoder *d);
 
 /* ---- uneven batches: several graphs in one launch --------------------------

@@ -27,6 +27,7 @@ MLD_EARLY_TERM, MLD_DEVICE_PTRS = 0x1, 0x2
 MLD_VN_GATHER, MLD_VN_ACCUMULATE = 0, 1
 MLD_SCHED_FLOODING, MLD_SCHED_LAYERED = 0, 1
 MLD_CHECK_SUM_PRODUCT, MLD_CHECK_MIN_SUM = 0, 1
+MLD_STAGE_DIRECT, MLD_STAGE_BULK, MLD_STAGE_BULK_LSU = 0, 1, 2
 
 # Offset (nats) of offset min-sum on the rate-0.1 ensemble: the smallest of
 # {0.3, 0.4, 0.5, 0.7, 1.0} that matched sum-product's frame error rate (0 of
@@ -63,7 +64,8 @@ class Opts(ctypes.Structure):
                 ("lmax", ctypes.c_float), ("slab_width", ctypes.c_int32),
                 ("vn_update", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("check_rule", ctypes.c_int32), ("ms_offset", ctypes.c_float),
-                ("checked", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("checked", ctypes.c_int32), ("staging", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class IndexArrays(ctypes.Structure):
@@ -316,12 +318,16 @@ class Decoder:
     ``schedule``: "flooding" (default) or "layered" (checks one layer at a
     time, see Graph.set_layers).
     ``check_rule``: "sum_product" (default) or "min_sum" (offset min-sum with
-    ``ms_offset`` nats)."""
+    ``ms_offset`` nats).
+    ``staging``: "direct" (default), "bulk" or "bulk_lsu" (check-update
+    operands staged in shared memory by bulk copies where that applies,
+    posterior rows by one bulk copy each or by per-thread cp.async; see
+    mld_opts)."""
 
     def __init__(self, graph: Graph, max_batch: int, msg_dtype: str = "f32",
                  lmax: float = 25.0, slab_width: int = 0, vn_update: str = "gather",
                  schedule: str = "flooding", check_rule: str = "sum_product",
-                 ms_offset: float = DEFAULT_MS_OFFSET, checked: bool = False):
+                 ms_offset: float = DEFAULT_MS_OFFSET, checked: bool = False, staging: str = "direct"):
         o = Opts()
         o.msg_dtype = {"f32": MLD_MSG_F32, "f16": MLD_MSG_F16}[msg_dtype]
         o.max_batch = int(max_batch)
@@ -332,6 +338,7 @@ class Decoder:
         o.check_rule = {"sum_product": MLD_CHECK_SUM_PRODUCT, "min_sum": MLD_CHECK_MIN_SUM}[check_rule]
         o.ms_offset = float(ms_offset) if check_rule == "min_sum" else 0.0
         o.checked = 1 if checked else 0
+        o.staging = {"direct": MLD_STAGE_DIRECT, "bulk": MLD_STAGE_BULK, "bulk_lsu": MLD_STAGE_BULK_LSU}[staging]
         h = ctypes.c_void_p()
         _check(lib().mld_decoder_create(graph.handle, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -143,6 +143,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     CnArgs ca{g->cptr, g->col, g->dptr, h.n_cn, h.n_core, h.n_deg1, h.e_core,
               d->r, d->Lv, d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done,
               d->lmax_i, d->amin_i, 0, et ? 1 : 0, 0, batch, d->hb1, d->fail};
+    ca.status = d->status;
     // early termination without soft output: degree-1 decisions only, and
     // the syndrome of iteration l-1 formed inside check pass l (every check
     // in a register class; otherwise a separate syndrome check per iteration)
@@ -173,6 +174,8 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, d->device);
     const dim3 syn_grid(syndrome_blocks(h.n_cn, sm_count), slabs);
     const int cap_blocks = sm_count * 16;  // two waves of 8 blocks per SM
+    // staged check updates: one wave of kStagedBlocksPerSm blocks per SM
+    const int staged_cap = d->staging != MLD_STAGE_DIRECT ? sm_count * kStagedBlocksPerSm : 0;
     const int lane_blocks = (batch + 127) / 128;
     const int64_t acc_n4 = static_cast<int64_t>(slabs) * h.n_core * W / 4;
     const int copy_blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((acc_n4 + kBlock - 1) / kBlock,
@@ -244,13 +247,13 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
                 }
             } else {
                 if (big < 0) {
-                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(c2, cl, slabs, s, cap_blocks, hard1);
+                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(c2, cl, slabs, s, cap_blocks, hard1, staged_cap, d->staging);
                 } else {
                     MLD_CUDA(cudaEventRecord(d->ev_fork, s));
                     MLD_CUDA(cudaStreamWaitEvent(d->side, d->ev_fork, 0));
-                    launch_check_class<MsgT, W>(c2, launches[big], slabs, s, cap_blocks, hard1);
+                    launch_check_class<MsgT, W>(c2, launches[big], slabs, s, cap_blocks, hard1, staged_cap, d->staging);
                     for (size_t i = 0; i < launches.size(); ++i)
-                        if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(c2, launches[i], slabs, d->side, cap_blocks, hard1);
+                        if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(c2, launches[i], slabs, d->side, cap_blocks, hard1, staged_cap, d->staging);
                     MLD_CUDA(cudaEventRecord(d->ev_join, d->side));
                     MLD_CUDA(cudaStreamWaitEvent(s, d->ev_join, 0));
                 }
@@ -399,7 +402,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
         {
             int s = timed_launch(d, kClsCheck, st, "k_check_update", [&] {
                 if (big < 0) {
-                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st, cap_blocks, hard1);
+                    for (const ClassLaunch &cl : launches) launch_check_class<MsgT, W>(ca, cl, slabs, st, cap_blocks, hard1, staged_cap, d->staging);
                     return;
                 }
                 // the largest class on the caller's stream; the others on the
@@ -407,9 +410,9 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
                 // drains (errors of the event calls surface as the launch error)
                 cudaEventRecord(d->ev_fork, st);
                 cudaStreamWaitEvent(d->side, d->ev_fork, 0);
-                launch_check_class<MsgT, W>(ca, launches[big], slabs, st, cap_blocks, hard1);
+                launch_check_class<MsgT, W>(ca, launches[big], slabs, st, cap_blocks, hard1, staged_cap, d->staging);
                 for (size_t i = 0; i < launches.size(); ++i)
-                    if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(ca, launches[i], slabs, d->side, cap_blocks, hard1);
+                    if (static_cast<int>(i) != big) launch_check_class<MsgT, W>(ca, launches[i], slabs, d->side, cap_blocks, hard1, staged_cap, d->staging);
                 cudaEventRecord(d->ev_join, d->side);
                 cudaStreamWaitEvent(st, d->ev_join, 0);
             }, static_cast<int>(launches.size()));
@@ -720,9 +723,11 @@ int mld_graph_layers_get(const mld_graph *g, int32_t *layer_of_check, int32_t *n
 int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **out) {
     mld::clear_error();
     if (!g || !opts || !out) return mld::fail(MLD_EINVAL, "decoder_create: null pointer");
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (opts->reserved[i] != 0) return mld::fail(MLD_EINVAL, "decoder_create: reserved field not zero");
     if (opts->checked != 0 && opts->checked != 1) return mld::fail(MLD_EINVAL, "decoder_create: checked must be 0 or 1");
+    if (opts->staging != MLD_STAGE_DIRECT && opts->staging != MLD_STAGE_BULK && opts->staging != MLD_STAGE_BULK_LSU)
+        return mld::fail(MLD_EINVAL, "decoder_create: unknown staging");
     if (opts->check_rule != MLD_CHECK_SUM_PRODUCT && opts->check_rule != MLD_CHECK_MIN_SUM)
         return mld::fail(MLD_EINVAL, "decoder_create: unknown check_rule");
     if (opts->check_rule == MLD_CHECK_MIN_SUM &&
@@ -761,6 +766,10 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     }
     int s = check_device(g->device);
     if (s != MLD_OK) return s;
+    if (opts->staging != MLD_STAGE_DIRECT) {
+        const cudaError_t ce = prepare_staged_kernels();
+        if (ce != cudaSuccess) return cuda_fail(ce, "decoder_create: staged kernels");
+    }
     if (opts->schedule == MLD_SCHED_LAYERED && !g->lchk) {
         // no layering given: the default first fit per check class
         s = mld_graph_set_layers(const_cast<mld_graph *>(g), nullptr, 0);
@@ -776,6 +785,7 @@ int mld_decoder_create(const mld_graph *g, const mld_opts *opts, mld_decoder **o
     d->schedule = opts->schedule;
     d->check_rule = opts->check_rule;
     d->checked = opts->checked != 0;
+    d->staging = opts->staging;
     d->ms_off_i = opts->check_rule == MLD_CHECK_MIN_SUM ? opts->ms_offset * 1.4426950408889634f : 0.f;
     d->max_batch = opts->max_batch;
     d->max_slabs = (opts->max_batch + W - 1) / W;
@@ -870,6 +880,8 @@ int mld_decode_status(mld_decoder *d) {
     int32_t v[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMemcpy(v, d->status, sizeof(v), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "decode_status");
+    if (v[0] == MLD_ETIMEOUT)
+        return mld::fail(MLD_ETIMEOUT, "decode_status: a staged check update gave up waiting for a bulk copy");
     return v[0] == 0 ? MLD_OK : mld::fail(v[0], graph_fault_text(v));
 }
 

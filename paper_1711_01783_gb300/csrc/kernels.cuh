@@ -254,6 +254,9 @@ struct CnArgs {
     // ms_off (internal units).
     int rule;
     float ms_off;
+    // Decoder status word (int32[4]); a staged check update whose bulk copy
+    // never completes records MLD_ETIMEOUT here.  May be null elsewhere.
+    int32_t *status;
 };
 
 enum { kRuleSumProduct = 0, kRuleMinSum = 1 };
@@ -325,32 +328,67 @@ constexpr uint32_t kSign = 0x80000000u;
 // not its posterior (early termination without soft output); with a.fuse the
 // call also returns the previous iteration's syndrome failures of the check
 // for the thread's 4 codewords (bit k: codeword lane0 + k), else 0.
+// Where a check's terms are read from.  TermsGlobal: straight from the
+// posterior, message and degree-1 arrays, the core VNs' column indices
+// loaded first; lv(i) / ro(i): posterior and stored message of core term i,
+// p1(i): phi term of degree-1 term i, each for the thread's 4 codewords.
+template <typename MsgT, int W, int DC>
+struct TermsGlobal {
+    const float *lvb;
+    const MsgT *rb;
+    const float *p1b;
+    int32_t e0, s0;
+    int32_t vidx[DC > 0 ? DC : 1];
+    __device__ __forceinline__ float4 lv(int i) const { return ldf4(lvb + static_cast<size_t>(vidx[i]) * W); }
+    __device__ __forceinline__ float4 ro(int i) const {
+        return Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
+    }
+    __device__ __forceinline__ float4 p1(int i) const { return ldf4(p1b + static_cast<size_t>(s0 + i) * W); }
+};
+
+template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC, typename Terms>
+__device__ __forceinline__ uint32_t check_terms(const CnArgs &a, int lane0, int slab, bool valid, int32_t e0,
+                                                int32_t s0, uint32_t sb, uint32_t donenib, const Terms &t);
+
 template <typename MsgT, int W, int DC, int DD, bool HARD1 = false, bool ACC = false>
 __device__ __forceinline__ uint32_t check_regular(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
                                                   int slab) {
     constexpr int NB = W / 8;
-    constexpr int D = DC + DD;
-    constexpr int dc = DC;
-    constexpr int F = DecodeFit<MsgT>::value;
     const int32_t count = cl.count;
     const bool valid = j < count;
     if (!valid) j = count - 1;
     const int32_t c = cl.c0 + j;
-    const int32_t e0 = cl.e0 + j * dc;
-    const int32_t s0 = cl.s0 + j * (D - dc);
-    const float lmax = a.lmax, amin = a.amin;
+    const int32_t e0 = cl.e0 + j * DC;
+    const int32_t s0 = cl.s0 + j * DD;
 
     const uint32_t sb =
         (static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + c) * NB + lane0 / 8]) >>
          (lane0 & 7));
     const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
-    MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
-    const float *lvb = a.Lv + static_cast<size_t>(slab) * a.n_core * W + lane0;
-    const float *p1b = a.phi1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
-
-    int32_t vidx[D];
+    TermsGlobal<MsgT, W, DC> t;
+    t.rb = static_cast<const MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
+    t.lvb = a.Lv + static_cast<size_t>(slab) * a.n_core * W + lane0;
+    t.p1b = a.phi1 + static_cast<size_t>(slab) * a.n_deg1 * W + lane0;
+    t.e0 = e0;
+    t.s0 = s0;
 #pragma unroll
-    for (int i = 0; i < D; ++i) vidx[i] = (i < dc) ? __ldg(a.col + e0 + i) : 0;
+    for (int i = 0; i < DC; ++i) t.vidx[i] = __ldg(a.col + e0 + i);
+    return check_terms<MsgT, W, DC, DD, HARD1, ACC>(a, lane0, slab, valid, e0, s0, sb, donenib, t);
+}
+
+// The update of one check from its terms (read through t), codewords lane0
+// .. lane0+3 of the slab; valid false: compute but store nothing.  sb: the
+// check's syndrome bits for the 4 codewords (bit k: lane0 + k); donenib:
+// their converged flags under early termination.
+template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC, typename Terms>
+__device__ __forceinline__ uint32_t check_terms(const CnArgs &a, int lane0, int slab, bool valid, int32_t e0,
+                                                int32_t s0, uint32_t sb, uint32_t donenib, const Terms &t) {
+    constexpr int NB = W / 8;
+    constexpr int D = DC + DD;
+    constexpr int dc = DC;
+    constexpr int F = DecodeFit<MsgT>::value;
+    const float lmax = a.lmax, amin = a.amin;
+    MsgT *rb = static_cast<MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W + lane0;
 
     // pass 1: f = phi(|q|) carrying the sign of q in its sign bit; the top
     // bit of par accumulates the sign parity (syndrome bit included).  For a
@@ -363,12 +401,12 @@ __device__ __forceinline__ uint32_t check_regular(const CnArgs &a, const ClassLa
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         if (i < dc) {
-            const float4 lv = ldf4(lvb + static_cast<size_t>(vidx[i]) * W);
+            const float4 lv = t.lv(i);
             if constexpr (HARD1) {
 #pragma unroll
                 for (int kk = 0; kk < kK; ++kk) lvs[kk] ^= fbits(f4get(lv, kk));
             }
-            const float4 ro = Msg<MsgT>::load(rb + static_cast<size_t>(e0 + i) * W);
+            const float4 ro = t.ro(i);
             const float4 q = make_float4(lv.x - ro.x, lv.y - ro.y, lv.z - ro.z, lv.w - ro.w);
             // phi(|q|) floored at amin = phi(lmax) is phi of |q| clamped above at
             // lmax.  |q| is not clamped below: an argument under phi(lmax)
@@ -384,7 +422,7 @@ __device__ __forceinline__ uint32_t check_regular(const CnArgs &a, const ClassLa
                 par[kk] ^= qb;
             }
         } else {
-            const float4 p = ldf4(p1b + static_cast<size_t>(s0 + i - dc) * W);
+            const float4 p = t.p1(i - dc);
 #pragma unroll
             for (int kk = 0; kk < kK; ++kk) {
                 f[i][kk] = f4get(p, kk);
@@ -612,6 +650,246 @@ __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? (ACC ? 7 : 8) : 6)) k_
                                                   static_cast<int32_t>(gridDim.x), slab);
 }
 
+// ---------------------------------------------------------------------------
+// Staged check update.  The classes of at most six terms can also run with
+// their operands brought into shared memory by the bulk-copy (TMA) engine
+// one stage ahead of the arithmetic: a stage is G consecutive checks of the
+// class (one per group of W/4 threads); its message rows and degree-1 terms
+// are two contiguous copies, its posterior rows one 16-byte-aligned copy per
+// core edge (issued by the thread that loaded that edge's column index a
+// stage earlier).  Completion is tracked by one mbarrier per buffer (two
+// buffers); the arithmetic is check_terms, reading shared memory.  Every
+// wait is bounded in time: a copy that has not landed after kWaitLimitNs
+// records MLD_ETIMEOUT in the status word and the block leaves, storing
+// nothing for that stage.
+// ---------------------------------------------------------------------------
+constexpr int kStagedBlocksPerSm = 6;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the phase of the given parity to complete; false after
+// kWaitLimitNs without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+// Orders this thread's earlier generic-proxy accesses of shared memory
+// before its later bulk copies into it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bulk copy global -> shared (both addresses 16-byte aligned, bytes a
+// multiple of 16), completing as transaction bytes on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 16-byte asynchronous copy global -> shared through the load/store unit
+// (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// Arrive on the mbarrier once this thread's earlier cp.async copies have
+// landed; counts as one of the phase's expected arrivals.
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <typename MsgT, int W, int DC, int DD>
+struct StageShape {
+    static constexpr int TPC = W / kK;                               // threads per check
+    static constexpr int G = kBlock / TPC;                           // checks per stage
+    static constexpr int kMsgRow = W * static_cast<int>(sizeof(MsgT));
+    static constexpr int kF32Row = W * 4;
+    static constexpr int kMsg = G * DC * kMsgRow;                    // message rows
+    static constexpr int kP1 = G * DD * kF32Row;                     // degree-1 terms
+    static constexpr int kPost = G * DC * kF32Row;                   // posterior rows
+    static constexpr int kStage = kMsg + kP1 + kPost;
+    static constexpr int kBytes = 2 * kStage + 2 * 8;                // two buffers, two mbarriers
+    static constexpr int kPerCheck = DC * kMsgRow + DD * kF32Row + DC * kF32Row;
+};
+
+// Terms of one check in a stage buffer (pointers already at the thread's
+// lane0).
+template <typename MsgT, int W>
+struct TermsShared {
+    const float *post;
+    const MsgT *msg;
+    const float *phi;
+    __device__ __forceinline__ float4 lv(int i) const { return *reinterpret_cast<const float4 *>(post + i * W); }
+    __device__ __forceinline__ float4 ro(int i) const { return Msg<MsgT>::load(msg + i * W); }
+    __device__ __forceinline__ float4 p1(int i) const { return *reinterpret_cast<const float4 *>(phi + i * W); }
+};
+
+// A capped grid; block b takes stages b, b + gridDim.x, ...  Sum-product,
+// no fused syndrome (HARD1 false), no accumulation.  LSU false: each
+// posterior row is one bulk copy, issued by the thread that loaded its
+// column index; LSU true: every thread copies its own 16 bytes of each of
+// its check's posterior rows with cp.async (the load/store unit, not the
+// bulk-copy engine) and signals the stage's mbarrier when they land.
+template <typename MsgT, int W, int DC, int DD, bool LSU>
+__global__ void __launch_bounds__(kBlock, kStagedBlocksPerSm) k_check_staged(CnArgs a, ClassLaunch cl) {
+    using S = StageShape<MsgT, W, DC, DD>;
+    static_assert(DC + DD > 0 && DD <= 1, "staged classes");
+    constexpr int NC = DC > 0 ? DC : 1;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int slab = blockIdx.y;
+    if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + 2 * S::kStage);
+    const int tid = threadIdx.x;
+    const int g = tid / S::TPC;
+    const int lane0 = (tid % S::TPC) * kK;
+    const int32_t count = cl.count;
+    const int32_t stages = (count + S::G - 1) / S::G;
+    const int32_t step = static_cast<int32_t>(gridDim.x);
+    if (tid == 0) {
+        // LSU: one arrival from thread 0 (with the byte count of the bulk
+        // copies) and one from each thread's cp.async group per phase
+        mbar_init(&full[0], LSU ? 1 + kBlock : 1);
+        mbar_init(&full[1], LSU ? 1 + kBlock : 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const MsgT *rsrc = static_cast<const MsgT *>(a.r) + static_cast<size_t>(slab) * a.e_core * W;
+    const float *lvsrc = a.Lv + static_cast<size_t>(slab) * a.n_core * W;
+    const float *p1src = a.phi1 + static_cast<size_t>(slab) * a.n_deg1 * W;
+    constexpr int NB = W / 8;
+    constexpr uint32_t kBulkPerCheck = LSU ? DC * S::kMsgRow + DD * S::kF32Row : S::kPerCheck;
+
+    // column indices for the posterior copies of stage st (-1: none).  Bulk:
+    // thread tid < G*DC takes row tid of the stage (check tid / DC, term
+    // tid % DC) in v[0].  LSU: a thread takes the DC rows of its own check.
+    auto cols_of = [&](int32_t st, int32_t (&v)[NC]) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) v[i] = -1;
+        if constexpr (DC > 0) {
+            if (st >= stages) return;
+            if constexpr (LSU) {
+                const int32_t j = st * S::G + g;
+                if (j < count) {
+#pragma unroll
+                    for (int i = 0; i < DC; ++i) v[i] = __ldg(a.col + cl.e0 + j * DC + i);
+                }
+            } else {
+                if (tid >= S::G * DC) return;
+                const int32_t j = st * S::G + tid / DC;
+                if (j < count) v[0] = __ldg(a.col + cl.e0 + j * DC + tid % DC);
+            }
+        }
+    };
+    auto sb_of = [&](int32_t st) -> uint32_t {
+        const int32_t j = min(st * S::G + g, count - 1);
+        return static_cast<uint32_t>(a.sbits[(static_cast<size_t>(slab) * a.n_cn + cl.c0 + j) * NB + lane0 / 8]) >>
+               (lane0 & 7);
+    };
+    auto issue = [&](int32_t st, int buf, const int32_t (&v)[NC]) {
+        unsigned char *base = smem + buf * S::kStage;
+        const int32_t j0 = st * S::G;
+        const int32_t nv = min(S::G, count - j0);
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&full[buf], static_cast<uint32_t>(nv) * kBulkPerCheck);
+            if (DC > 0)
+                bulk_g2s(base, rsrc + static_cast<size_t>(cl.e0 + j0 * DC) * W,
+                         static_cast<uint32_t>(nv * DC * S::kMsgRow), &full[buf]);
+            if (DD > 0)
+                bulk_g2s(base + S::kMsg, p1src + static_cast<size_t>(cl.s0 + j0 * DD) * W,
+                         static_cast<uint32_t>(nv * DD * S::kF32Row), &full[buf]);
+        }
+        if constexpr (LSU) {
+            float *post = reinterpret_cast<float *>(base + S::kMsg + S::kP1) + g * DC * W + lane0;
+#pragma unroll
+            for (int i = 0; i < DC; ++i)
+                if (v[i] >= 0) cp_async16(post + i * W, lvsrc + static_cast<size_t>(v[i]) * W + lane0);
+            cp_async_arrive_noinc(&full[buf]);
+        } else {
+            if (v[0] >= 0) {
+                if (tid != 0) fence_proxy_async_smem();
+                bulk_g2s(base + S::kMsg + S::kP1 + tid * S::kF32Row, lvsrc + static_cast<size_t>(v[0]) * W,
+                         static_cast<uint32_t>(S::kF32Row), &full[buf]);
+            }
+        }
+    };
+
+    int32_t s = static_cast<int32_t>(blockIdx.x);
+    int32_t vn[NC];
+    cols_of(s, vn);
+    if (s < stages) issue(s, 0, vn);
+    cols_of(s + step, vn);
+    uint32_t sbn = s < stages ? sb_of(s) : 0u;
+    const uint32_t donenib = a.et ? done_nibble<W>(a.done, slab, lane0) : 0u;
+    for (int k = 0; s < stages; s += step, ++k) {
+        const int buf = k & 1;
+        const int32_t sn = s + step;
+        // the other buffer was released by the barrier that ended the
+        // previous stage
+        if (sn < stages) issue(sn, buf ^ 1, vn);
+        cols_of(sn + step, vn);
+        const uint32_t sb = sbn;
+        if (sn < stages) sbn = sb_of(sn);
+        const bool ok = mbar_wait(&full[buf], static_cast<uint32_t>(k >> 1) & 1u);
+        int32_t j = s * S::G + g;
+        const bool valid = ok && j < count;
+        if (j >= count) j = count - 1;
+        const unsigned char *base = smem + buf * S::kStage;
+        TermsShared<MsgT, W> t;
+        t.msg = reinterpret_cast<const MsgT *>(base) + g * DC * W + lane0;
+        t.phi = reinterpret_cast<const float *>(base + S::kMsg) + g * DD * W + lane0;
+        t.post = reinterpret_cast<const float *>(base + S::kMsg + S::kP1) + g * DC * W + lane0;
+        check_terms<MsgT, W, DC, DD, false, false>(a, lane0, slab, valid, cl.e0 + j * DC, cl.s0 + j * DD, sb,
+                                                   donenib, t);
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: record it, give the copies in flight
+            // (this stage's and the next one's) a bounded time to land, leave
+            if (tid == 0) {
+                if (a.status) atomicCAS(a.status, 0, MLD_ETIMEOUT);
+                mbar_wait(&full[buf], static_cast<uint32_t>(k >> 1) & 1u);
+                if (sn < stages) mbar_wait(&full[buf ^ 1], static_cast<uint32_t>((k + 1) >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+    }
+}
+
+template <typename MsgT, int W>
+constexpr bool kStagedWidth = IsHalf<MsgT>::value && W == 64;
+
 // Posterior accumulation is built for the default slab width of each
 // message type (64 half, 32 float).
 template <typename MsgT, int W>
@@ -635,13 +913,75 @@ __global__ void __launch_bounds__(kBlock) k_check_update_irregular(CnArgs a, Cla
 template <typename MsgT, int W>
 void launch_minsum_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks);
 
+// Six staged blocks per SM need the largest shared-memory carveout; set once
+// per kernel (a function attribute, not stream work) when a decoder that
+// stages is created.
+template <typename MsgT, int W, int DC, int DD>
+cudaError_t prefer_smem_staged() {
+    cudaError_t e = cudaFuncSetAttribute(k_check_staged<MsgT, W, DC, DD, false>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_check_staged<MsgT, W, DC, DD, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared);
+}
+
+inline cudaError_t prepare_staged_kernels() {
+    const cudaError_t e[] = {
+        prefer_smem_staged<__half, 64, 1, 0>(), prefer_smem_staged<__half, 64, 2, 0>(),
+        prefer_smem_staged<__half, 64, 3, 0>(), prefer_smem_staged<__half, 64, 4, 0>(),
+        prefer_smem_staged<__half, 64, 5, 0>(), prefer_smem_staged<__half, 64, 6, 0>(),
+        prefer_smem_staged<__half, 64, 0, 1>(), prefer_smem_staged<__half, 64, 1, 1>(),
+        prefer_smem_staged<__half, 64, 2, 1>(), prefer_smem_staged<__half, 64, 3, 1>(),
+        prefer_smem_staged<__half, 64, 4, 1>(), prefer_smem_staged<__half, 64, 5, 1>()};
+    for (cudaError_t x : e)
+        if (x != cudaSuccess) return x;
+    return cudaSuccess;
+}
+
+template <typename MsgT, int W, int DC, int DD>
+void launch_staged(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int staged_cap,
+                   int mode) {
+    using S = StageShape<MsgT, W, DC, DD>;
+    static_assert(S::kBytes <= 48 * 1024, "staged buffers within the default dynamic shared memory");
+    const int32_t stages = (cl.count + S::G - 1) / S::G;
+    const dim3 grid(std::max(1, std::min<int32_t>(stages, staged_cap)), slabs);
+    if (mode == MLD_STAGE_BULK_LSU) k_check_staged<MsgT, W, DC, DD, true><<<grid, kBlock, S::kBytes, st>>>(ca, cl);
+    else k_check_staged<MsgT, W, DC, DD, false><<<grid, kBlock, S::kBytes, st>>>(ca, cl);
+}
+
+// The staged kernel, where it applies (half messages at slab width 64,
+// sum-product, no fused syndrome, no accumulation, a register class of at
+// most six terms with at most one degree-1 VN per check); false otherwise.
+template <typename MsgT, int W>
+bool try_launch_staged(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int staged_cap,
+                       bool hard1, int mode) {
+    if constexpr (kStagedWidth<MsgT, W>) {
+        const int dd = cl.deg - cl.dc;
+        if (staged_cap <= 0 || hard1 || ca.acc || ca.rule != kRuleSumProduct || cl.dc < 0 || cl.deg > 6 ||
+            cl.count <= 0 || (dd != 0 && dd != 1))
+            return false;
+        switch (cl.dc * 2 + dd) {
+#define MLD_STAGED(DCV, DDV) \
+    case (DCV) * 2 + (DDV): launch_staged<MsgT, W, DCV, DDV>(ca, cl, slabs, st, staged_cap, mode); return true;
+            MLD_STAGED(1, 0) MLD_STAGED(2, 0) MLD_STAGED(3, 0) MLD_STAGED(4, 0) MLD_STAGED(5, 0) MLD_STAGED(6, 0)
+            MLD_STAGED(0, 1) MLD_STAGED(1, 1) MLD_STAGED(2, 1) MLD_STAGED(3, 1) MLD_STAGED(4, 1) MLD_STAGED(5, 1)
+#undef MLD_STAGED
+            default: return false;
+        }
+    } else {
+        (void)ca; (void)cl; (void)slabs; (void)st; (void)staged_cap; (void)hard1; (void)mode;
+        return false;
+    }
+}
+
 template <typename MsgT, int W>
 void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cudaStream_t st, int cap_blocks,
-                        bool hard1) {
+                        bool hard1, int staged_cap = 0, int staged_mode = MLD_STAGE_DIRECT) {
     if (ca.rule == kRuleMinSum) {
         launch_minsum_class<MsgT, W>(ca, cl, slabs, st, cap_blocks);
         return;
     }
+    if (try_launch_staged<MsgT, W>(ca, cl, slabs, st, staged_cap, hard1, staged_mode)) return;
     const dim3 grid(cl.blocks, slabs);
     const dim3 capped(std::max(1, std::min(cl.blocks, cap_blocks)), slabs);
     const dim3 g = (cl.dc >= 0 && cl.deg <= 6) ? capped : grid;
@@ -1730,6 +2070,7 @@ struct mld_decoder {
     int check_rule = MLD_CHECK_SUM_PRODUCT;
     float ms_off_i = 0.f;  // min-sum offset, internal units
     int checked = 0;       // validate the graph store before every decode
+    int staging = MLD_STAGE_DIRECT;  // check-update operands: direct or bulk-staged
     int32_t *status_host = nullptr;  // page-locked copy of the status word
     // early termination run by the device: capture stream, iteration counter
     // and cap (device), and the loop graphs built so far (per batch size,
