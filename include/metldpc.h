@@ -344,6 +344,17 @@ int mld_decode_y(mld_decoder *d, const float *y, const float *sigma,
  * status word with a blocking copy; call after the stream is idle. */
 int mld_decode_status(mld_decoder *d);
 
+/* Test of the timeout path of the staged check update: with bytes > 0, every
+ * later staged check-update launch of this decoder makes one block expect
+ * `bytes` more than its first stage's copies bring, so that block's bounded
+ * wait (2 s) runs out, it records MLD_ETIMEOUT in the status word and leaves
+ * without storing (the decode's results are then invalid); 0 turns it off.
+ * No fault is raised and the context stays usable.  Decoders without staging
+ * ignore it.  A change waits for the device to be idle (it drops the
+ * decoder's captured early-termination loops).  Errors: MLD_EINVAL (null
+ * decoder, bytes outside [0, 65536]), MLD_ECUDA. */
+int mld_decoder_test_stall(mld_decoder *d, int32_t bytes);
+
 /* ---- uneven batches: several graphs in one launch --------------------------
  * A job is a batch of codewords of one graph, decoded with its own decoder
  * (which fixes the graph, message storage type, slab width and working

@@ -40,7 +40,7 @@ _STATUS = {MLD_EINVAL: "MLD_EINVAL", MLD_ENOMEM: "MLD_ENOMEM", MLD_ECUDA: "MLD_E
 # Every symbol include/metldpc.h declares.
 EXPORTS = ("mld_last_error", "mld_version", "mld_graph_create", "mld_graph_destroy",
            "mld_graph_stats_get", "mld_decoder_create", "mld_decoder_destroy", "mld_decode",
-           "mld_decode_y", "mld_decode_status", "mld_decoder_timing_enable",
+           "mld_decode_y", "mld_decode_status", "mld_decoder_test_stall", "mld_decoder_timing_enable",
            "mld_decoder_timing_read", "mld_decode_noalloc", "mld_plan_create", "mld_plan_launch",
            "mld_plan_stats", "mld_plan_destroy", "mld_decode_multi", "mld_wbp_forward", "mld_wbp_backward",
            "mld_tape_destroy", "mld_phi_eval", "mld_ensemble_size", "mld_ensemble_edges",
@@ -113,6 +113,7 @@ def _load() -> ctypes.CDLL:
         "mld_decode": (ctypes.c_int, [P, P, P, I32, I32, U32, P, P, P, P, P]),
         "mld_decode_y": (ctypes.c_int, [P, P, P, P, I32, I32, U32, P, P, P, P, P]),
         "mld_decode_status": (ctypes.c_int, [P]),
+        "mld_decoder_test_stall": (ctypes.c_int, [P, ctypes.c_int32]),
         "mld_decoder_timing_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "mld_decoder_timing_read": (ctypes.c_int, [P, ctypes.POINTER(Timing)]),
         "mld_decode_noalloc": (ctypes.c_int, [P, I32, P, P, I32, I32, U32, P, P, P, P, P]),
@@ -423,6 +424,10 @@ class Decoder:
 
     def status(self) -> int:
         return int(lib().mld_decode_status(self._h))
+
+    def test_stall(self, nbytes: int) -> None:
+        """Timeout-path test hook (mld_decoder_test_stall)."""
+        _check(lib().mld_decoder_test_stall(self._h, int(nbytes)))
 
     def wbp_forward(self, llr, syndrome, weights, ckpt_k: int = 5, keep_tape: bool = True, stream=None):
         """Weighted BP forward (mld_wbp_forward); returns (soft [B, n], Tape or None)."""

@@ -144,6 +144,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
               d->r, d->Lv, d->lch1, d->phi1, d->post1, d->hb1, d->sbits, d->done,
               d->lmax_i, d->amin_i, 0, et ? 1 : 0, 0, batch, d->hb1, d->fail};
     ca.status = d->status;
+    ca.stall_test = d->stall_test;
     // early termination without soft output: degree-1 decisions only, and
     // the syndrome of iteration l-1 formed inside check pass l (every check
     // in a register class; otherwise a separate syndrome check per iteration)
@@ -883,6 +884,21 @@ int mld_decode_status(mld_decoder *d) {
     if (v[0] == MLD_ETIMEOUT)
         return mld::fail(MLD_ETIMEOUT, "decode_status: a staged check update gave up waiting for a bulk copy");
     return v[0] == 0 ? MLD_OK : mld::fail(v[0], graph_fault_text(v));
+}
+
+int mld_decoder_test_stall(mld_decoder *d, int32_t bytes) {
+    mld::clear_error();
+    if (!d) return mld::fail(MLD_EINVAL, "decoder_test_stall: null decoder");
+    if (bytes < 0 || bytes > 65536) return mld::fail(MLD_EINVAL, "decoder_test_stall: bytes outside [0, 65536]");
+    if (bytes != d->stall_test && !d->loops.empty()) {
+        // the early-termination loop graphs hold the launch arguments they
+        // were captured with: drop them (after the device is idle)
+        MLD_CUDA(cudaDeviceSynchronize());
+        for (auto &lg : d->loops) cudaGraphExecDestroy(lg.exec);
+        d->loops.clear();
+    }
+    d->stall_test = bytes;
+    return MLD_OK;
 }
 
 int mld_decoder_timing_enable(mld_decoder *d, int enable) {

@@ -257,6 +257,10 @@ struct CnArgs {
     // Decoder status word (int32[4]); a staged check update whose bulk copy
     // never completes records MLD_ETIMEOUT here.  May be null elsewhere.
     int32_t *status;
+    // Test of the timeout path: bytes added to the byte count that block
+    // (0, 0) of a staged check update expects for its first stage, so that
+    // its wait runs out (0: none).
+    int32_t stall_test;
 };
 
 enum { kRuleSumProduct = 0, kRuleMinSum = 1 };
@@ -696,14 +700,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 // Waits for the phase of the given parity to complete; false after
-// kWaitLimitNs without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// limit_ns without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
+// After a wait has run out: how long to give the copies still in flight.
+constexpr unsigned long long kDrainNs = 100000000ull;
 // Orders this thread's earlier generic-proxy accesses of shared memory
 // before its later bulk copies into it.
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -823,7 +830,9 @@ __global__ void __launch_bounds__(kBlock, kStagedBlocksPerSm) k_check_staged(CnA
         const int32_t nv = min(S::G, count - j0);
         if (tid == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&full[buf], static_cast<uint32_t>(nv) * kBulkPerCheck);
+            const uint32_t extra =
+                (a.stall_test > 0 && blockIdx.x == 0 && blockIdx.y == 0 && st == 0) ? a.stall_test : 0;
+            mbar_arrive_expect_tx(&full[buf], static_cast<uint32_t>(nv) * kBulkPerCheck + extra);
             if (DC > 0)
                 bulk_g2s(base, rsrc + static_cast<size_t>(cl.e0 + j0 * DC) * W,
                          static_cast<uint32_t>(nv * DC * S::kMsgRow), &full[buf]);
@@ -878,8 +887,8 @@ __global__ void __launch_bounds__(kBlock, kStagedBlocksPerSm) k_check_staged(CnA
             // (this stage's and the next one's) a bounded time to land, leave
             if (tid == 0) {
                 if (a.status) atomicCAS(a.status, 0, MLD_ETIMEOUT);
-                mbar_wait(&full[buf], static_cast<uint32_t>(k >> 1) & 1u);
-                if (sn < stages) mbar_wait(&full[buf ^ 1], static_cast<uint32_t>((k + 1) >> 1) & 1u);
+                mbar_wait(&full[buf], static_cast<uint32_t>(k >> 1) & 1u, kDrainNs);
+                if (sn < stages) mbar_wait(&full[buf ^ 1], static_cast<uint32_t>((k + 1) >> 1) & 1u, kDrainNs);
             }
             __syncthreads();
             return;
@@ -2071,6 +2080,7 @@ struct mld_decoder {
     float ms_off_i = 0.f;  // min-sum offset, internal units
     int checked = 0;       // validate the graph store before every decode
     int staging = MLD_STAGE_DIRECT;  // check-update operands: direct or bulk-staged
+    int32_t stall_test = 0;          // mld_decoder_test_stall
     int32_t *status_host = nullptr;  // page-locked copy of the status word
     // early termination run by the device: capture stream, iteration counter
     // and cap (device), and the loop graphs built so far (per batch size,

@@ -103,3 +103,15 @@ def test_noalloc_binding_rejects_bad_arguments_before_the_library(mld):
         mld.decode_noalloc(g, good_l, _FakeCuda((3, 4), torch.uint8, device="cuda:1"), 5)
     with pytest.raises(ValueError):
         mld.decode_noalloc(g, good_l, good_s, 5, msg_dtype="bf16")
+
+
+def test_staging_and_stall_hook_are_declared(mld):
+    """The staging constants and the timeout test hook are in the header and
+    the binding (no GPU call)."""
+    m = mld
+    hdr = open(HEADER).read()
+    for name, val in (("MLD_STAGE_DIRECT", 0), ("MLD_STAGE_BULK", 1), ("MLD_STAGE_BULK_LSU", 2)):
+        assert re.search(rf"#define {name}\s+{val}\b", hdr)
+        assert getattr(m, name) == val
+    assert "int mld_decoder_test_stall(mld_decoder *d, int32_t bytes);" in hdr
+    assert [f for f, _ in m.Opts._fields_][-3:] == ["checked", "staging", "reserved"]

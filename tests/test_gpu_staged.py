@@ -124,3 +124,36 @@ def test_full_size_headline_shape(mld, mode):
     _same(o1, o2)
     assert np.array_equal(_syndrome_holds(w.graph, _np(o2["bits"]), w.s), _np(o2["converged"]).astype(bool))
     assert staged.status() == 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_timeout_path(mld, mode):
+    """A stage whose mbarrier expects 16 bytes more than its copies bring
+    (mld_decoder_test_stall): block (0, 0) of each staged launch waits 2 s,
+    records MLD_ETIMEOUT and leaves without storing; no fault, and the
+    context keeps decoding correctly with a fresh decoder."""
+    import time
+    w = make_workload(0.1, 4096, 64, 1, 8500)
+    g = mld.Graph.from_edges(w.graph)
+    args = (_dev(w.y), _dev(w.sigma), _dev(w.s))
+    dec = mld.Decoder(g, 64, msg_dtype="f16", staging=mode)
+    dec.decode_y(*args, iters=1)
+    torch.cuda.synchronize()
+    assert dec.status() == 0
+    dec.test_stall(16)
+    t0 = time.time()
+    dec.decode_y(*args, iters=1)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    assert dec.status() == mld.MLD_ETIMEOUT
+    assert 1.9 < dt < 60, dt
+    # the status is sticky for that decoder; a new one is clean and exact
+    assert dec.status() == mld.MLD_ETIMEOUT
+    _, direct, staged = _pair(mld, w.graph, 64, mode)
+    o1 = direct.decode_y(*args, iters=5, want_post=True)
+    o2 = staged.decode_y(*args, iters=5, want_post=True)
+    torch.cuda.synchronize()
+    _same(o1, o2)
+    assert staged.status() == 0
+    with pytest.raises(mld.MldError):
+        dec.test_stall(-1)
