@@ -350,11 +350,11 @@ struct TermsGlobal {
     __device__ __forceinline__ float4 p1(int i) const { return ldf4(p1b + static_cast<size_t>(s0 + i) * W); }
 };
 
-template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC, typename Terms>
+template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC, bool FUSE, typename Terms>
 __device__ __forceinline__ uint32_t check_terms(const CnArgs &a, int lane0, int slab, bool valid, int32_t e0,
                                                 int32_t s0, uint32_t sb, uint32_t donenib, const Terms &t);
 
-template <typename MsgT, int W, int DC, int DD, bool HARD1 = false, bool ACC = false>
+template <typename MsgT, int W, int DC, int DD, bool HARD1 = false, bool ACC = false, bool FUSE = HARD1>
 __device__ __forceinline__ uint32_t check_regular(const CnArgs &a, const ClassLaunch &cl, int32_t j, int lane0,
                                                   int slab) {
     constexpr int NB = W / 8;
@@ -377,14 +377,14 @@ __device__ __forceinline__ uint32_t check_regular(const CnArgs &a, const ClassLa
     t.s0 = s0;
 #pragma unroll
     for (int i = 0; i < DC; ++i) t.vidx[i] = __ldg(a.col + e0 + i);
-    return check_terms<MsgT, W, DC, DD, HARD1, ACC>(a, lane0, slab, valid, e0, s0, sb, donenib, t);
+    return check_terms<MsgT, W, DC, DD, HARD1, ACC, FUSE>(a, lane0, slab, valid, e0, s0, sb, donenib, t);
 }
 
 // The update of one check from its terms (read through t), codewords lane0
 // .. lane0+3 of the slab; valid false: compute but store nothing.  sb: the
 // check's syndrome bits for the 4 codewords (bit k: lane0 + k); donenib:
 // their converged flags under early termination.
-template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC, typename Terms>
+template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC, bool FUSE, typename Terms>
 __device__ __forceinline__ uint32_t check_terms(const CnArgs &a, int lane0, int slab, bool valid, int32_t e0,
                                                 int32_t s0, uint32_t sb, uint32_t donenib, const Terms &t) {
     constexpr int NB = W / 8;
@@ -406,7 +406,7 @@ __device__ __forceinline__ uint32_t check_terms(const CnArgs &a, int lane0, int 
     for (int i = 0; i < D; ++i) {
         if (i < dc) {
             const float4 lv = t.lv(i);
-            if constexpr (HARD1) {
+            if constexpr (HARD1 && FUSE) {
 #pragma unroll
                 for (int kk = 0; kk < kK; ++kk) lvs[kk] ^= fbits(f4get(lv, kk));
             }
@@ -513,7 +513,7 @@ __device__ __forceinline__ uint32_t check_terms(const CnArgs &a, int lane0, int 
         }
     }
     uint32_t fail = 0;
-    if constexpr (HARD1) {
+    if constexpr (HARD1 && FUSE) {
         if (a.fuse && valid) {
             // previous iteration: s_c XOR the decisions of the check's VNs
             // (core: posterior < 0, the sign read above; degree-1: stored bit)
@@ -622,7 +622,7 @@ template <int D> constexpr bool kLoopedClass = D <= 6;
 // The threads of a class launch (t0: thread index in the slab's grid of
 // `blocks` blocks): looped classes step through their checks, the others take
 // one; with HARD1 the fused syndrome failures are ORed into a.fail_prev.
-template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC = false>
+template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC = false, bool FUSE = HARD1>
 __device__ __forceinline__ void check_class_body(const CnArgs &a, const ClassLaunch &cl, int64_t t0,
                                                  int32_t blocks, int slab) {
     constexpr int TPC = W / kK;
@@ -634,22 +634,25 @@ __device__ __forceinline__ void check_class_body(const CnArgs &a, const ClassLau
         // threads of a shuffle pair belong to one check and leave together.
         const int32_t jstride = blocks * (kBlock / TPC);
         for (int32_t j = static_cast<int32_t>(t0 / TPC); j < cl.count; j += jstride)
-            fail |= check_regular<MsgT, W, DC, DD, HARD1, ACC>(a, cl, j, lane0, slab);
+            fail |= check_regular<MsgT, W, DC, DD, HARD1, ACC, FUSE>(a, cl, j, lane0, slab);
     } else {
-        fail = check_regular<MsgT, W, DC, DD, HARD1, ACC>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
+        fail = check_regular<MsgT, W, DC, DD, HARD1, ACC, FUSE>(a, cl, static_cast<int32_t>(t0 / TPC), lane0, slab);
     }
-    if constexpr (HARD1) {
+    if constexpr (HARD1 && FUSE) {
         if (a.fuse) flush_fail<W>(a.fail_prev + slab * ((W + 31) / 32), fail, lane0);
     }
 }
 
 // One check class per launch, its shape (DC, DD) a compile-time constant: the
 // register arrays are sized exactly and only this class's code is hot.
-template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC = false>
-__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? (ACC ? 7 : 8) : 6)) k_check_update(CnArgs a, ClassLaunch cl) {
+// HARD1 without FUSE (decisions only, the syndrome checked by its own
+// kernel): 7 blocks per SM, 72 registers without spills.
+template <typename MsgT, int W, int DC, int DD, bool HARD1, bool ACC = false, bool FUSE = HARD1>
+__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? ((ACC || (HARD1 && !FUSE)) ? 7 : 8) : 6))
+    k_check_update(CnArgs a, ClassLaunch cl) {
     const int slab = blockIdx.y;
     if (a.et && slab_all_done<W>(a.done, slab)) return;  // block-uniform
-    check_class_body<MsgT, W, DC, DD, HARD1, ACC>(a, cl,
+    check_class_body<MsgT, W, DC, DD, HARD1, ACC, FUSE>(a, cl,
                                                   static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
                                                   static_cast<int32_t>(gridDim.x), slab);
 }
@@ -880,7 +883,7 @@ __global__ void __launch_bounds__(kBlock, kStagedBlocksPerSm) k_check_staged(CnA
         t.msg = reinterpret_cast<const MsgT *>(base) + g * DC * W + lane0;
         t.phi = reinterpret_cast<const float *>(base + S::kMsg) + g * DD * W + lane0;
         t.post = reinterpret_cast<const float *>(base + S::kMsg + S::kP1) + g * DC * W + lane0;
-        check_terms<MsgT, W, DC, DD, false, false>(a, lane0, slab, valid, cl.e0 + j * DC, cl.s0 + j * DD, sb,
+        check_terms<MsgT, W, DC, DD, false, false, false>(a, lane0, slab, valid, cl.e0 + j * DC, cl.s0 + j * DD, sb,
                                                    donenib, t);
         if (__syncthreads_or(!ok)) {
             // a copy never completed: record it, give the copies in flight
@@ -994,6 +997,10 @@ void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cuda
     const dim3 grid(cl.blocks, slabs);
     const dim3 capped(std::max(1, std::min(cl.blocks, cap_blocks)), slabs);
     const dim3 g = (cl.dc >= 0 && cl.deg <= 6) ? capped : grid;
+    // the decisions-only kernels without the fused syndrome run 7 blocks per
+    // SM: their looped grid is two waves of 7
+    const dim3 capped7(std::max(1, std::min(cl.blocks, cap_blocks / 8 * 7)), slabs);
+    const dim3 g7 = (cl.dc >= 0 && cl.deg <= 6) ? capped7 : grid;
     const int dd = cl.deg - cl.dc;
 #define MLD_CASE(DCV, DDV)                                                                          \
     case (DCV) * 2 + (DDV):                                                                         \
@@ -1004,7 +1011,8 @@ void launch_check_class(const CnArgs &ca, const ClassLaunch &cl, int slabs, cuda
                 return;                                                                             \
             }                                                                                       \
         }                                                                                           \
-        if (hard1) k_check_update<MsgT, W, DCV, DDV, true><<<g, kBlock, 0, st>>>(ca, cl);          \
+        if (hard1 && ca.fuse) k_check_update<MsgT, W, DCV, DDV, true><<<g, kBlock, 0, st>>>(ca, cl); \
+        else if (hard1) k_check_update<MsgT, W, DCV, DDV, true, false, false><<<g7, kBlock, 0, st>>>(ca, cl); \
         else k_check_update<MsgT, W, DCV, DDV, false><<<g, kBlock, 0, st>>>(ca, cl);              \
         return;
     if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
