@@ -307,9 +307,15 @@ __device__ __forceinline__ void emit_deg1_bits(const CnArgs &a, int slab, int sl
     if (valid && (lane0 & 7) == 0) *hb = static_cast<uint8_t>(nib | (other << 4));
 }
 
-template <typename MsgT, int W>
+// Message store under early termination: converged lanes keep their
+// messages frozen.  The freeze is not needed for exact outputs (a converged
+// codeword's posterior and decisions are frozen by the variable update and
+// emit_deg1*, and no output reads its later messages), so the
+// decisions-only kernels skip it (FREEZE false), which saves a reload and
+// four selects per term once lanes have converged.
+template <typename MsgT, int W, bool FREEZE = true>
 __device__ __forceinline__ void store_r(const CnArgs &a, MsgT *rp, float4 rv, uint32_t donenib) {
-    if (donenib) {  // converged lanes keep their messages frozen
+    if (FREEZE && donenib) {
         const float4 old = Msg<MsgT>::load(rp);
         if (donenib & 1) rv.x = old.x;
         if (donenib & 2) rv.y = old.y;
@@ -497,7 +503,7 @@ __device__ __forceinline__ uint32_t check_terms(const CnArgs &a, int lane0, int 
                             float *ap = a.acc + (static_cast<size_t>(slab) * a.n_core + v) * W + lane0;
                             atomicAdd(reinterpret_cast<float4 *>(ap), st);
                         } else if (a.et) {
-                            store_r<MsgT, W>(a, rp, rv, donenib);
+                            store_r<MsgT, W, !HARD1>(a, rp, rv, donenib);
                         } else {
                             Msg<MsgT>::store(rp, rv);
                         }
