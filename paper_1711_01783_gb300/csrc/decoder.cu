@@ -238,7 +238,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
                     const int blocks = std::max(1, std::min(grid_x(static_cast<int64_t>(ll.count) * TPC),
                                                             sm_count * kLayeredBlocksPerSm));
                     ClassLaunch cl{k.c0, ll.count, k.dc, k.dc + k.dd, ll.e0, k.s0, blocks};
-                    launch_layered<MsgT, W>(la, cl, g->lchk + ll.p0, slabs, s);
+                    launch_layered<MsgT, W>(la, cl, g->lchk + ll.p0, slabs, s, hard1);
                 }
                 MLD_LAUNCHED("k_check_layered");
                 if (h.n_core > 0) {
@@ -364,7 +364,7 @@ int run_decode(mld_decoder *d, const float *in, const float *sigma, const uint8_
                     const int blocks = std::max(1, std::min(grid_x(static_cast<int64_t>(ll.count) * TPC),
                                                             sm_count * kLayeredBlocksPerSm));
                     ClassLaunch cl{k.c0, ll.count, k.dc, k.dc + k.dd, ll.e0, k.s0, blocks};
-                    launch_layered<MsgT, W>(la, cl, g->lchk + ll.p0, slabs, st);
+                    launch_layered<MsgT, W>(la, cl, g->lchk + ll.p0, slabs, st, hard1);
                 }
             }, static_cast<int>(n_launch));
             if (s != MLD_OK) return s;

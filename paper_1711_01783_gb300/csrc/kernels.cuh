@@ -1070,8 +1070,10 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStre
 // ---------------------------------------------------------------------------
 // Layered launches number their messages contiguously: the launch's k-th
 // check (internal id c) owns layered edges cl.e0 + k DC ..; a.col is the
-// layered column table.  Its degree-1 slots follow the class order.
-template <typename MsgT, int W, int DC, int DD>
+// layered column table.  Its degree-1 slots follow the class order.  HARD1:
+// a degree-1 VN gets its decision only (early termination without soft
+// output), as in check_terms.
+template <typename MsgT, int W, int DC, int DD, bool HARD1 = false>
 __device__ __forceinline__ void check_layered(const CnArgs &a, const ClassLaunch &cl, int32_t c, int32_t k,
                                               int lane0, int slab, bool valid) {
     constexpr int D = DC + DD;
@@ -1138,6 +1140,20 @@ __device__ __forceinline__ void check_layered(const CnArgs &a, const ClassLaunch
                 else v = pre[i][kk] + suf[kk];
                 f4set(o, kk, v);
             }
+            if (HARD1 && i >= DC) {
+                // decision of L_ch + r without r: see check_terms
+                uint32_t nib = 0;
+#pragma unroll
+                for (int kk = 0; kk < kK; ++kk) {
+                    const uint32_t fb = fbits(f[i][kk]);
+                    const bool l_neg = (fb & kSign) != 0;
+                    const bool r_neg = ((par[kk] ^ fb) & kSign) != 0;
+                    const float fl = fabsf(f[i][kk]), ov = f4get(o, kk);
+                    const bool neg = (l_neg == r_neg) ? l_neg : (l_neg ? fl < ov : fl > ov);
+                    nib |= static_cast<uint32_t>(neg) << kk;
+                }
+                emit_deg1_bits<W>(a, slab, s0 + i - DC, lane0, nib, donenib, valid);
+            } else {
             float4 mm = phi4_floor<F>(o, amin);
             if (D <= 2) mm = make_float4(fminf(mm.x, lmax), fminf(mm.y, lmax), fminf(mm.z, lmax), fminf(mm.w, lmax));
             float4 rv;
@@ -1170,6 +1186,7 @@ __device__ __forceinline__ void check_layered(const CnArgs &a, const ClassLaunch
             } else {
                 emit_deg1<MsgT, W>(a, slab, s0 + i - DC, lane0, rv, donenib, valid);
             }
+            }
         }
         if (i > 0) {
 #pragma unroll
@@ -1185,7 +1202,7 @@ __device__ __forceinline__ void check_layered(const CnArgs &a, const ClassLaunch
 // Blocks per SM of the layered kernels (72 registers per thread).
 constexpr int kLayeredBlocksPerSm = 7;
 
-template <typename MsgT, int W, int DC, int DD>
+template <typename MsgT, int W, int DC, int DD, bool HARD1>
 __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? kLayeredBlocksPerSm : 6))
     k_check_layered(CnArgs a, ClassLaunch cl, const int32_t *pos) {
     constexpr int TPC = W / kK;
@@ -1196,7 +1213,7 @@ __global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? kLayeredBlocksPerSm : 
     const int lane0 = static_cast<int>(t % TPC) * kK;
     const int32_t kstride = static_cast<int32_t>(gridDim.x) * (kBlock / TPC);
     for (int32_t k = static_cast<int32_t>(t / TPC); k < cl.count; k += kstride)
-        check_layered<MsgT, W, DC, DD>(a, cl, __ldg(pos + k), k, lane0, slab, true);
+        check_layered<MsgT, W, DC, DD, HARD1>(a, cl, __ldg(pos + k), k, lane0, slab, true);
 }
 
 // Layered update of a check of any degree (edges read through cptr/dptr);
@@ -1299,13 +1316,15 @@ __global__ void __launch_bounds__(kBlock) k_check_layered_irregular(CnArgs a, Cl
 // type.  Classes of at most 8 terms with at most one degree-1 VN run the
 // register kernel of their shape, any other class the runtime-degree kernel.
 template <typename MsgT, int W>
-void launch_layered(const CnArgs &ca, const ClassLaunch &cl, const int32_t *pos, int slabs, cudaStream_t st) {
+void launch_layered(const CnArgs &ca, const ClassLaunch &cl, const int32_t *pos, int slabs, cudaStream_t st,
+                    bool hard1) {
     if constexpr (kAccWidth<MsgT, W>) {
         const dim3 grid(cl.blocks, slabs);
         const int dd = cl.deg - cl.dc;
-#define MLD_LCASE(DCV, DDV)                                                                    \
-    case (DCV) * 2 + (DDV):                                                                    \
-        launch_pdl(k_check_layered<MsgT, W, DCV, DDV>, grid, dim3(kBlock), st, ca, cl, pos);  \
+#define MLD_LCASE(DCV, DDV)                                                                          \
+    case (DCV) * 2 + (DDV):                                                                          \
+        if (hard1) launch_pdl(k_check_layered<MsgT, W, DCV, DDV, true>, grid, dim3(kBlock), st, ca, cl, pos); \
+        else launch_pdl(k_check_layered<MsgT, W, DCV, DDV, false>, grid, dim3(kBlock), st, ca, cl, pos);     \
         return;
         if (cl.dc >= 0 && (dd == 0 || dd == 1)) {
             switch (cl.dc * 2 + dd) {
