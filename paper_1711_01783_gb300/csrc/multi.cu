@@ -61,8 +61,10 @@ __device__ __forceinline__ CnArgs job_cn(const JobDev &j, const Seg &sg, int32_t
     return a;
 }
 
+// The decisions-only form (with the fused syndrome) runs 7 blocks per SM:
+// at 8 its posterior-sign bookkeeping spills.
 template <typename MsgT, int W, int DC, int DD, bool HARD1>
-__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? 8 : 6))
+__global__ void __launch_bounds__(kBlock, (DC + DD <= 6 ? (HARD1 ? 7 : 8) : 6))
     km_check(const JobDev *jobs, const Seg *segs, int nseg, int32_t l) {
     const Seg sg = segs[find_seg(segs, nseg)];
     const CnArgs a = job_cn<W>(jobs[sg.job], sg, l);
@@ -422,11 +424,13 @@ int build_plan(const mld_job *jobs, int32_t n_jobs, uint32_t flags, mld_plan *p,
             for (const ClassLaunch &cl : d->g->launches[width_index(d->W)]) {
                 const int dd = cl.deg - cl.dc;
                 const bool regular = cl.dc >= 0 && (dd == 0 || dd == 1);
-                // looped register classes (at most 6 terms) run on a capped grid
+                // looped register classes (at most 6 terms) run on a capped
+                // grid of two waves (7 blocks per SM for the decisions-only form)
                 const bool looped = regular && cl.deg <= 6;
-                Seg s = seg(j, looped ? std::max(1, std::min(cl.blocks, sm_count * 16)) : cl.blocks, jd[j].slabs, fl);
-                s.cl = cl;
                 const int hard1 = (hard1_job(j) && regular) ? 1 : 0;
+                const int cap = sm_count * (hard1 ? 14 : 16);
+                Seg s = seg(j, looped ? std::max(1, std::min(cl.blocks, cap)) : cl.blocks, jd[j].slabs, fl);
+                s.cl = cl;
                 groups[Key{kOpCheck, half, d->W, regular ? cl.dc : -1, regular ? dd : -1, hard1}].push_back(s);
             }
             if (fused_job(j) && l >= 2) lanes.push_back(j);
