@@ -229,3 +229,26 @@ def test_layer_structured_ensemble(mld, n, B, beta, iters, sample):
         print(f"n={n} {msg}: structured layered converged {conv.sum()}/{B}, mean iterations "
               f"{_np(out['iters_used']).mean():.2f} (oracle {ref['iters_used'].mean():.2f})")
         dec.close()
+
+
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_early_termination_decisions_only(mld, msg):
+    """Layered decode without soft output: a degree-1 VN's decision compares
+    the leave-one-out sum with phi(|L_ch|) instead of taking the sign of
+    L_ch + phi(o) (no posterior stored).  Against the layered oracle with
+    the near-threshold criteria, and against the soft-output run: frames
+    both decode agree bit for bit, converged flags on >= 90 %."""
+    w = make_workload(0.1, 4096, 32, 1, 1310, beta=0.36)
+    g, dec, od = _layered(mld, w.graph, 32, msg)
+    args = (_dev(w.y), _dev(w.sigma), _dev(w.s))
+    soft = dec.decode_y(*args, iters=40, early_term=True, want_post=True)
+    hard = dec.decode_y(*args, iters=40, early_term=True)
+    assert hard.get("post") is None
+    ref = oracle.decode_layered(w.graph, oracle.channel_llr(w.y, w.sigma), w.s, iters=40, order=od,
+                                early_term=True)
+    _check_frames(hard, ref, w.graph, w.s, msg, near_threshold=True)
+    both = _np(soft["converged"]).astype(bool) & _np(hard["converged"]).astype(bool)
+    assert (_np(soft["converged"]) == _np(hard["converged"])).mean() >= 0.9
+    assert np.array_equal(_np(soft["bits"])[both], _np(hard["bits"])[both])
+    print(f"{msg}: decisions-only converged {int(_np(hard['converged']).sum())}/32, soft-output "
+          f"{int(_np(soft['converged']).sum())}/32, oracle {int(ref['converged'].sum())}/32")
