@@ -18,7 +18,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmetldpc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["decoder.cu", "multi.cu", "wbp.cu", "md.cu", "graph.cpp", "ensemble.cpp", "peg.cpp"]
+SOURCES = ["decoder.cu", "decode_f16.cu", "decode_f32.cu", "multi.cu", "wbp.cu", "md.cu", "graph.cpp",
+           "ensemble.cpp", "peg.cpp"]
 
 
 def nvcc() -> str:

@@ -2140,6 +2140,20 @@ struct mld_decoder {
     std::vector<cudaEvent_t> event_pool;
 };
 
+namespace mld {
+// decode_f16.cu / decode_f32.cu: one decode call's launch sequence for each
+// message storage type (separate translation units, compiled in parallel).
+int run_decode_f16(mld_decoder *d, const float *in, const float *sigma, const uint8_t *syn, int32_t batch,
+                   int32_t iters, bool et, uint8_t *bits, float *post, uint8_t *conv, int32_t *it,
+                   cudaStream_t st, bool out_dev);
+int run_decode_f32(mld_decoder *d, const float *in, const float *sigma, const uint8_t *syn, int32_t batch,
+                   int32_t iters, bool et, uint8_t *bits, float *post, uint8_t *conv, int32_t *it,
+                   cudaStream_t st, bool out_dev);
+// Sets the shared-memory carveout of the staged kernels that decode_f16.cu
+// launches (a function attribute belongs to one translation unit's kernel).
+cudaError_t prepare_staged_f16();
+}  // namespace mld
+
 namespace {
 
 // Sets the clamps and the nats <-> bits scales of a decoder from its lmax.
