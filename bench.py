@@ -80,11 +80,12 @@ DEFAULT_ITERS = {0.1: 100, 0.05: 150, 0.02: 200}
 TIMING_EVERY = 10
 
 # DRAM bytes (read + write) of one check-update pass per (codeword x bit),
-# from `ncu --set full` of the three check-class launches of one iteration
-# (rate 0.1, n = 3e5, 64 codewords, half messages: 396.62 MB); traffic
-# grows with n, so it is scaled by the units a full pass processes.  Valid
-# for the kernel of this commit only (see profiles/).
-CHECK_PASS_TRAFFIC_PER_CW_BIT = {(0.1, "f16"): 396.62e6 / (64 * 3e5)}
+# from ncu's dram__bytes_read.sum + dram__bytes_write.sum of the three
+# check-class launches of one iteration (rate 0.1, n = 3e5, 64 codewords,
+# half messages: 396.83 MB); traffic grows with n, so it is scaled by the
+# units a full pass processes.  Valid for the kernel of this commit only
+# (see profiles/).
+CHECK_PASS_TRAFFIC_PER_CW_BIT = {(0.1, "f16"): 396.83e6 / (64 * 3e5)}
 
 
 def algorithmic_bytes(st: dict, msg: str, schedule: str = "flooding") -> tuple[float, float]:
