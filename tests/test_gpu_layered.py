@@ -252,3 +252,29 @@ def test_early_termination_decisions_only(mld, msg):
     assert np.array_equal(_np(soft["bits"])[both], _np(hard["bits"])[both])
     print(f"{msg}: decisions-only converged {int(_np(hard['converged']).sum())}/32, soft-output "
           f"{int(_np(soft['converged']).sum())}/32, oracle {int(ref['converged'].sum())}/32")
+
+
+@pytest.mark.parametrize("rate", [0.05, 0.02])
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_other_rates_against_the_layered_oracle(mld, rate, msg):
+    """The check shapes of the rate-0.05 and rate-0.02 ensembles (4 to 6
+    terms) in the layered kernels: one iteration within the bounds of the
+    one-iteration test, then 30 iterations with early termination against
+    the layered oracle (per-frame criteria)."""
+    w = make_workload(rate, 20000, 8, 3, 6400, beta=0.30)
+    g, dec, od = _layered(mld, w.graph, 8, msg)
+    L = _llr32(w)
+    out = dec.decode(_dev(L), _dev(w.s), iters=1, want_post=True)
+    ref = oracle.decode_layered(w.graph, L, w.s, iters=1, order=od)
+    d = np.abs(_np(out["post"]).astype(np.float64) - ref["post"])
+    if msg == "f32":
+        bound = 2 * (1e-4 + 1e-5 * np.abs(ref["post"]))
+    else:
+        dv = w.graph.vn_degree()[None, :]
+        bound = 2 * (dv * ((2.0 ** -11 + 2.3e-4) * 25.0 + 2.3e-4) + 1e-4)
+    assert np.all(d <= bound), (d.max(), (d - bound).max())
+    out = dec.decode(_dev(L), _dev(w.s), iters=30, early_term=True, want_post=True)
+    ref = oracle.decode_layered(w.graph, L, w.s, iters=30, order=od, early_term=True)
+    _check_frames(out, ref, w.graph, w.s, msg, near_threshold=True)
+    print(f"rate {rate} {msg}: layers {g.layers()[1]}, one-iteration |dL| max {d.max():.3g}; converged "
+          f"{int(_np(out['converged']).sum())}/8 (oracle {int(ref['converged'].sum())}/8)")

@@ -111,3 +111,29 @@ def test_minsum_rejects_unsupported_decoders(mld):
         mld.Decoder(g, 8, check_rule="min_sum", schedule="layered")
     with pytest.raises(mld.MldError):
         mld.Decoder(g, 8, check_rule="min_sum", ms_offset=-1.0)
+
+
+@pytest.mark.parametrize("rate", [0.05, 0.02])
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_other_rates_against_the_minsum_oracle(mld, rate, msg):
+    """The check shapes of the rate-0.05 and rate-0.02 ensembles in the
+    min-sum kernels (several checks per thread at n = 2e4): one iteration
+    within the one-iteration bounds, then 30 iterations with early
+    termination against the min-sum oracle."""
+    w = make_workload(rate, 20000, 8, 3, 8800, beta=0.25)
+    g = mld.Graph.from_edges(w.graph)
+    dec = mld.Decoder(g, 8, msg_dtype=msg, check_rule="min_sum", ms_offset=OFF)
+    L = _llr32(w)
+    out = dec.decode(_dev(L), _dev(w.s), iters=1, want_post=True)
+    ref = oracle.decode_ms(w.graph, L, w.s, iters=1, offset=OFF)
+    d = np.abs(_np(out["post"]).astype(np.float64) - ref["post"])
+    if msg == "f32":
+        bound = 1e-4 + 1e-5 * np.abs(ref["post"])
+    else:
+        bound = w.graph.vn_degree()[None, :] * (2.0 ** -11 * 25.0) + 1e-4
+    assert np.all(d <= bound), (d.max(), (d - bound).max())
+    out = dec.decode(_dev(L), _dev(w.s), iters=30, early_term=True, want_post=True)
+    ref = oracle.decode_ms(w.graph, L, w.s, iters=30, offset=OFF, early_term=True)
+    _check_frames(out, ref, w.graph, w.s, msg, near_threshold=True)
+    print(f"rate {rate} {msg}: min-sum one-iteration |dL| max {d.max():.3g}; converged "
+          f"{int(_np(out['converged']).sum())}/8 (oracle {int(ref['converged'].sum())}/8)")
