@@ -1564,21 +1564,23 @@ __device__ __forceinline__ void var_body(const VnArgs &a, int64_t t, int slab) {
     float4 acc = ldf4(a.lch + vrow);
     int32_t j = a.vptr[v];
     const int32_t j1 = a.vptr[v + 1];
-    for (; j + 4 <= j1; j += 4) {
-        const int32_t ea = __ldg(a.vedge + j), eb = __ldg(a.vedge + j + 1);
-        const int32_t ec = __ldg(a.vedge + j + 2), ed = __ldg(a.vedge + j + 3);
+    // four edges per round, every load of a round in flight together; the
+    // last round's missing edges re-read the round's first row (an L1 hit)
+    // and add nothing, so the sums are formed in CSC order as before
+    for (; j < j1; j += 4) {
+        const int32_t rem = j1 - j;
+        const int32_t ea = __ldg(a.vedge + j);
+        const int32_t eb = rem > 1 ? __ldg(a.vedge + j + 1) : ea;
+        const int32_t ec = rem > 2 ? __ldg(a.vedge + j + 2) : ea;
+        const int32_t ed = rem > 3 ? __ldg(a.vedge + j + 3) : ea;
         const float4 ra = Msg<MsgT>::load(rb + static_cast<size_t>(ea) * W);
         const float4 rbv = Msg<MsgT>::load(rb + static_cast<size_t>(eb) * W);
         const float4 rc = Msg<MsgT>::load(rb + static_cast<size_t>(ec) * W);
         const float4 rd = Msg<MsgT>::load(rb + static_cast<size_t>(ed) * W);
         acc.x += ra.x; acc.y += ra.y; acc.z += ra.z; acc.w += ra.w;
-        acc.x += rbv.x; acc.y += rbv.y; acc.z += rbv.z; acc.w += rbv.w;
-        acc.x += rc.x; acc.y += rc.y; acc.z += rc.z; acc.w += rc.w;
-        acc.x += rd.x; acc.y += rd.y; acc.z += rd.z; acc.w += rd.w;
-    }
-    for (; j < j1; ++j) {
-        const float4 ra = Msg<MsgT>::load(rb + static_cast<size_t>(__ldg(a.vedge + j)) * W);
-        acc.x += ra.x; acc.y += ra.y; acc.z += ra.z; acc.w += ra.w;
+        if (rem > 1) { acc.x += rbv.x; acc.y += rbv.y; acc.z += rbv.z; acc.w += rbv.w; }
+        if (rem > 2) { acc.x += rc.x; acc.y += rc.y; acc.z += rc.z; acc.w += rc.w; }
+        if (rem > 3) { acc.x += rd.x; acc.y += rd.y; acc.z += rd.z; acc.w += rd.w; }
     }
     if (a.et) {
         // converged lanes keep the posterior of their last iteration (with a
