@@ -12,7 +12,10 @@ fastest per decoded codeword, and caches the choice in a JSON file keyed by
 termination to the variable-update variant as well: the gather pass or the
 accumulation of the new messages inside the check update (which wins with
 float messages and loses with half ones on GB300), over the slab widths each
-variant allows.  Plans keep the gather, so they use ``SlabWidthTuner``.
+variant allows, and for half messages to the staged check update (operands
+brought into shared memory by bulk copies; slower on GB300, where the
+direct kernel is instruction-bound).  Plans keep the gather, so they use
+``SlabWidthTuner``.
 """
 from __future__ import annotations
 
@@ -82,6 +85,9 @@ class DecoderTuner(SlabWidthTuner):
         default_w = 64 if msg_dtype == "f16" else 32
         out = [dict(slab_width=w, vn_update="gather") for w in WIDTHS]
         out.append(dict(slab_width=default_w, vn_update="accumulate"))
+        if msg_dtype == "f16":
+            # check-update operands staged in shared memory (half, width 64)
+            out += [dict(slab_width=64, vn_update="gather", staging=m) for m in ("bulk", "bulk_lsu")]
         return out
 
     def choose_options(self, graph, batch: int, msg_dtype: str = "f16") -> dict:
