@@ -335,9 +335,10 @@ constexpr uint32_t kSign = 0x80000000u;
 // terms in registers), codewords lane0 .. lane0+3 of the slab.  A thread past
 // the class end works on its last check and stores nothing (so a whole
 // shuffle pair stays active).  HARD1: a degree-1 VN gets its decision only,
-// not its posterior (early termination without soft output); with a.fuse the
-// call also returns the previous iteration's syndrome failures of the check
-// for the thread's 4 codewords (bit k: codeword lane0 + k), else 0.
+// not its posterior (early termination without soft output); FUSE (with
+// HARD1): with a.fuse the call also returns the previous iteration's
+// syndrome failures of the check for the thread's 4 codewords (bit k:
+// codeword lane0 + k), else 0.
 // Where a check's terms are read from.  TermsGlobal: straight from the
 // posterior, message and degree-1 arrays, the core VNs' column indices
 // loaded first; lv(i) / ro(i): posterior and stored message of core term i,
