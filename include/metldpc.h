@@ -429,6 +429,11 @@ int mld_decode_multi(const mld_job *jobs, int32_t n_jobs, uint32_t flags, void *
  * mld_wbp_backward: dsoft = dloss/dsoft_out (device float [batch][n_vn]);
  *   writes dw (device float [T][n_types]) and dllr (device float
  *   [batch][n_vn], 0 where the LLR was clamped).  May be called more than once.
+ * mld_tape_destroy: the decoder keeps the tape's device buffers (without
+ *   waiting for the device) and reuses them in its next mld_wbp_forward of
+ *   the same shape (batch slabs, T, ckpt_k, n_types), so a training loop
+ *   allocates once; that forward must be ordered after the backward's work
+ *   (same stream, or synchronised).  The decoder frees them when destroyed.
  * Checks of degree above 16 are refused (MLD_EINVAL).  Errors: MLD_EINVAL,
  * MLD_ENOMEM, MLD_ECUDA. */
 typedef struct mld_tape mld_tape;

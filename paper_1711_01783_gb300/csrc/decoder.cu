@@ -72,6 +72,7 @@ namespace {
 
 void decoder_free(mld_decoder *d) {
     if (!d) return;
+    mld::tape_release(d);
     if (d->r) cudaFree(d->r);
     d->r = nullptr;
     dfree(d->Lv); dfree(d->lch); dfree(d->lch1); dfree(d->post1); dfree(d->phi1);

@@ -2116,6 +2116,8 @@ struct mld_decoder {
     float ms_off_i = 0.f;  // min-sum offset, internal units
     int checked = 0;       // validate the graph store before every decode
     int staging = MLD_STAGE_DIRECT;  // check-update operands: direct or bulk-staged
+    // weighted BP: the tape in use, and the buffers of the last destroyed one
+    mld_tape *tape_live = nullptr, *tape_spare = nullptr;
     int32_t stall_test = 0;          // mld_decoder_test_stall
     int32_t *status_host = nullptr;  // page-locked copy of the status word
     // early termination run by the device: capture stream, iteration counter
@@ -2155,6 +2157,8 @@ int run_decode_f32(mld_decoder *d, const float *in, const float *sigma, const ui
 // Sets the shared-memory carveout of the staged kernels that decode_f16.cu
 // launches (a function attribute belongs to one translation unit's kernel).
 cudaError_t prepare_staged_f16();
+// wbp.cu: frees a decoder's spare weighted-BP tape, detaches a live one.
+void tape_release(mld_decoder *d);
 }  // namespace mld
 
 namespace {

@@ -602,7 +602,30 @@ int wbp_backward_w(mld_tape *tp, const float *dsoft, float *dw, float *dllr, cud
 template <typename T>
 int talloc(T **p, size_t n) { return dalloc(p, n); }
 
+// A decoder keeps the buffers of its last destroyed tape and hands them to
+// the next forward of the same shape, so a training loop allocates (and
+// frees, which waits for the device) once instead of every step.
+mld_tape *take_spare(mld_decoder *d, int32_t slabs, int32_t T, int32_t k, int32_t n_types) {
+    mld_tape *tp = d->tape_spare;
+    if (!tp) return nullptr;
+    d->tape_spare = nullptr;
+    if (tp->slabs == slabs && tp->T == T && tp->k == k && tp->n_types == n_types) return tp;
+    tape_free(tp);
+    return nullptr;
+}
+
 }  // namespace
+
+namespace mld {
+// Decoder teardown: frees the spare tape and detaches a tape still alive (it
+// frees its own buffers when destroyed).
+void tape_release(mld_decoder *d) {
+    if (d->tape_spare) tape_free(d->tape_spare);
+    d->tape_spare = nullptr;
+    if (d->tape_live) d->tape_live->d = nullptr;
+    d->tape_live = nullptr;
+}
+}  // namespace mld
 
 extern "C" {
 
@@ -631,6 +654,17 @@ int mld_wbp_forward(mld_decoder *d, const float *llr, const uint8_t *syndrome, i
     mld_tape *tp = nullptr;
     const float *wdev = w;
     if (tape) {
+        tp = take_spare(d, slabs, T, std::min(ckpt_k, T), n_types);
+        if (tp) {
+            tp->batch = batch;
+            cudaError_t e = cudaMemcpyAsync(tp->w, w, sizeof(float) * T * n_types, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) {
+                tape_free(tp);
+                return cuda_fail(e, "wbp_forward: copy weights");
+            }
+        }
+    }
+    if (tape && !tp) {
         tp = new (std::nothrow) mld_tape();
         if (!tp) return mld::fail(MLD_ENOMEM, "wbp_forward: host allocation");
         tp->d = d;
@@ -667,8 +701,8 @@ int mld_wbp_forward(mld_decoder *d, const float *llr, const uint8_t *syndrome, i
             tape_free(tp);
             return s;
         }
-        wdev = tp->w;
     }
+    if (tp) wdev = tp->w;
     switch (W) {
         case 8: s = wbp_forward_w<8>(d, llr, syndrome, batch, T, tp, wdev, n_types, soft_out, st); break;
         case 16: s = wbp_forward_w<16>(d, llr, syndrome, batch, T, tp, wdev, n_types, soft_out, st); break;
@@ -679,7 +713,10 @@ int mld_wbp_forward(mld_decoder *d, const float *llr, const uint8_t *syndrome, i
         tape_free(tp);
         return s;
     }
-    if (tape) *tape = tp;
+    if (tape) {
+        *tape = tp;
+        d->tape_live = tp;
+    }
     return MLD_OK;
 }
 
@@ -698,6 +735,13 @@ int mld_wbp_backward(mld_tape *tp, const float *dsoft, float *dw, float *dllr, v
 }
 
 int mld_tape_destroy(mld_tape *tp) {
+    if (!tp) return MLD_OK;
+    mld_decoder *d = tp->d;
+    if (d && d->tape_live == tp) d->tape_live = nullptr;
+    if (d && !d->tape_spare) {
+        d->tape_spare = tp;  // buffers kept for the next forward of this shape
+        return MLD_OK;
+    }
     tape_free(tp);
     return MLD_OK;
 }

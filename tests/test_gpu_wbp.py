@@ -121,3 +121,25 @@ def test_training_lowers_the_loss(mld):
         opt.step()
         losses.append(float(loss.detach()))
     assert losses[-1] < losses[0]
+
+
+def test_reused_tape_buffers_give_the_same_gradients(mld):
+    """A destroyed tape's buffers serve the decoder's next forward of the
+    same shape: repeated forward + backward calls (and a change of T and of
+    ckpt_k in between, which takes fresh buffers) give the gradients of a
+    decoder used once."""
+    rng = np.random.default_rng(5)
+    g0, w, L, dec = _setup(mld, 4096, 8, 0.45, 3)
+    results = {}
+    for T, k in ((8, 3), (8, 3), (6, 2), (8, 3), (8, 3)):
+        Wt = 1.0 + 0.05 * rng.standard_normal((T, 3))
+        key = (T, k, float(Wt.sum()))
+        got = _loss_and_grads(mld, dec, L, w.s, w.x, Wt, k)
+        fresh = _setup(mld, 4096, 8, 0.45, 3)[3]
+        ref = _loss_and_grads(mld, fresh, L, w.s, w.x, Wt, k)
+        fresh.close()
+        assert got[0] == ref[0], key
+        for a, b in zip(got[1:], ref[1:]):
+            np.testing.assert_array_equal(a, b)
+        results[key] = got[0]
+    assert len(results) == 5
