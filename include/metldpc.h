@@ -434,6 +434,10 @@ int mld_decode_multi(const mld_job *jobs, int32_t n_jobs, uint32_t flags, void *
  *   the same shape (batch slabs, T, ckpt_k, n_types), so a training loop
  *   allocates once; that forward must be ordered after the backward's work
  *   (same stream, or synchronised).  The decoder frees them when destroyed.
+ *   With a tape, the forward's iterations and the adjoint's segments run as
+ *   CUDA graphs over the tape's buffers, captured (on the decoder's own
+ *   capture stream) at the tape's first use and replayed later; if this
+ *   thread cannot capture, they are launched directly.
  * Checks of degree above 16 are refused (MLD_EINVAL).  Errors: MLD_EINVAL,
  * MLD_ENOMEM, MLD_ECUDA. */
 typedef struct mld_tape mld_tape;

@@ -442,17 +442,57 @@ struct mld_tape {
     float *glch = nullptr, *glch1 = nullptr, *gd1 = nullptr;
     float *gwp = nullptr;
     int gwp_blocks = 0;
+    // The iterations of the forward and the segments of the adjoint, as
+    // CUDA graphs over this tape's (and its decoder's) fixed buffers:
+    // captured at first use, replayed by later calls with this tape.
+    cudaGraphExec_t fwd_exec = nullptr, bwd_exec = nullptr;
+    float *dw = nullptr;  // [T][n_types], copied to the caller's dw
 };
 
 namespace {
 
 void tape_free(mld_tape *t) {
     if (!t) return;
+    if (t->fwd_exec) cudaGraphExecDestroy(t->fwd_exec);
+    if (t->bwd_exec) cudaGraphExecDestroy(t->bwd_exec);
+    dfree(t->dw);
     dfree(t->w);
     for (float *&p : t->ckpt) dfree(p);
     dfree(t->seg_r); dfree(t->seg_lv); dfree(t->gr); dfree(t->gx);
     dfree(t->glch); dfree(t->glch1); dfree(t->gd1); dfree(t->gwp);
     delete t;
+}
+
+// Enqueues `enqueue(stream)` on st through the CUDA graph *exec: captured
+// on the decoder's capture stream the first time (so that a few hundred
+// small launches become one), replayed after.  Where capture is not
+// possible (no capture stream, or another capture owns this thread) the
+// work is launched directly.
+template <typename F>
+int run_graph(mld_decoder *d, cudaGraphExec_t *exec, cudaStream_t st, F &&enqueue) {
+    if (!*exec) {
+        if (!d->cap) return enqueue(st);
+        cudaError_t e = cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return enqueue(st);
+        }
+        const int s = enqueue(d->cap);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(d->cap, &gr);
+        if (s != MLD_OK || ec != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            return s != MLD_OK ? s : cuda_fail(ec, "weighted BP: graph capture");
+        }
+        e = cudaGraphInstantiate(exec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            *exec = nullptr;
+            return cuda_fail(e, "weighted BP: graph instantiation");
+        }
+    }
+    MLD_CUDA(cudaGraphLaunch(*exec, st));
+    return MLD_OK;
 }
 
 WArgs wargs(const mld_decoder *d, const float *w, int n_types) {
@@ -509,7 +549,13 @@ int wbp_forward_w(mld_decoder *d, const float *llr, const uint8_t *syn, int32_t 
         MLD_LAUNCHED("k_syndrome_in");
     }
     const WArgs wa = wargs(d, w, n_types);
-    int s = forward_iters<W>(d, wa, static_cast<float *>(d->r), d->Lv, 0, T, T, slabs, st, tape, nullptr, nullptr);
+    auto iters = [&](cudaStream_t s2) {
+        return forward_iters<W>(d, wa, static_cast<float *>(d->r), d->Lv, 0, T, T, slabs, s2, tape, nullptr,
+                                nullptr);
+    };
+    // with a tape every buffer the iterations touch is fixed for the tape's
+    // life (the weights were copied into it), so they run as a graph
+    int s = tape ? run_graph(d, &tape->fwd_exec, st, iters) : iters(st);
     if (s != MLD_OK) return s;
     OutArgs oa{d->g->unit, h.n_vn, h.n_core, h.n_deg1, batch, d->Lv, d->post1, d->hb1, nullptr, 0, d->bits_stage,
                soft, 1.f};
@@ -543,54 +589,62 @@ int wbp_backward_w(mld_tape *tp, const float *dsoft, float *dw, float *dllr, cud
             dsoft, d->g->unit, h.n_vn, h.n_core, h.n_deg1, tp->batch, tp->glch, tp->glch1, tp->gd1);
         MLD_LAUNCHED("kw_interleave");
     }
-    if (h.n_core > 0) {
-        kw_grad_edges<W><<<vgrid, kBlock, 0, st>>>(wa, tp->glch, tp->gr);
-        MLD_LAUNCHED("kw_grad_edges");
-    }
-    float *r = static_cast<float *>(d->r);
-    for (int t0 = ((T - 1) / K) * K; t0 >= 0; t0 -= K) {
-        const int t1 = std::min(t0 + K, T);
-        // recompute r^{t0} .. r^{t1-1} and L^{t0} .. L^{t1-1}
-        if (t0 == 0) {
-            if (rsz) MLD_CUDA(cudaMemsetAsync(r, 0, rsz * sizeof(float), st));
-        } else {
-            MLD_CUDA(cudaMemcpyAsync(r, tp->ckpt[t0 / K - 1], rsz * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        }
+    // from dL^T on, every buffer is the tape's or the decoder's: the
+    // segments run as a graph (dw into the tape, then copied out)
+    auto segments = [&](cudaStream_t s2) -> int {
         if (h.n_core > 0) {
-            VnArgs va{d->g->vptr, d->g->vedge, h.n_core, h.e_core, r, d->lch, d->Lv, d->hb_core, d->done, 0, 0};
-            k_var_update<float, W><<<vgrid, kBlock, 0, st>>>(va);
-            MLD_LAUNCHED("k_var_update");
+            kw_grad_edges<W><<<vgrid, kBlock, 0, s2>>>(wa, tp->glch, tp->gr);
+            MLD_LAUNCHED("kw_grad_edges");
         }
-        int s = forward_iters<W>(d, wa, r, d->Lv, t0, t1 - 1, T, slabs, st, tp, tp->seg_r, tp->seg_lv);
-        if (s != MLD_OK) return s;
-        // r^{t1-1}, L^{t1-1} are now in r / d->Lv; store them as the last segment entry
-        MLD_CUDA(cudaMemcpyAsync(tp->seg_r + (t1 - 1 - t0) * rsz, r, rsz * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        MLD_CUDA(cudaMemcpyAsync(tp->seg_lv + (t1 - 1 - t0) * lsz, d->Lv, lsz * sizeof(float),
-                                 cudaMemcpyDeviceToDevice, st));
-        for (int t = t1; t > t0; --t) {
-            const float *rp = tp->seg_r + (t - 1 - t0) * rsz;
-            const float *lvp = tp->seg_lv + (t - 1 - t0) * lsz;
-            if (parts > 0) {
-                int32_t part0 = 0;
-                for (const mld::ClassLaunch &cl : classes) {
-                    launch_check_bwd<W>(wa, cl, rp, lvp, tp->gr, t == T ? tp->gd1 : nullptr, tp->gx, tp->glch1,
-                                        tp->gwp, t, slabs, part0, st);
-                    MLD_LAUNCHED("kw_check_bwd");
-                    part0 += cl.blocks * slabs;
-                }
-                kw_reduce_dw<<<1, kReduceThreads, 0, st>>>(tp->gwp, parts, tp->n_types,
-                                                           dw + static_cast<size_t>(t - 1) * tp->n_types);
-                MLD_LAUNCHED("kw_reduce_dw");
+        float *r = static_cast<float *>(d->r);
+        for (int t0 = ((T - 1) / K) * K; t0 >= 0; t0 -= K) {
+            const int t1 = std::min(t0 + K, T);
+            // recompute r^{t0} .. r^{t1-1} and L^{t0} .. L^{t1-1}
+            if (t0 == 0) {
+                if (rsz) MLD_CUDA(cudaMemsetAsync(r, 0, rsz * sizeof(float), s2));
             } else {
-                MLD_CUDA(cudaMemsetAsync(dw + static_cast<size_t>(t - 1) * tp->n_types, 0,
-                                         sizeof(float) * tp->n_types, st));
+                MLD_CUDA(cudaMemcpyAsync(r, tp->ckpt[t0 / K - 1], rsz * sizeof(float), cudaMemcpyDeviceToDevice, s2));
             }
             if (h.n_core > 0) {
-                kw_var_bwd<W><<<vgrid, kBlock, 0, st>>>(wa, tp->gx, tp->glch, t > 1 ? tp->gr : nullptr);
-                MLD_LAUNCHED("kw_var_bwd");
+                VnArgs va{d->g->vptr, d->g->vedge, h.n_core, h.e_core, r, d->lch, d->Lv, d->hb_core, d->done, 0, 0};
+                k_var_update<float, W><<<vgrid, kBlock, 0, s2>>>(va);
+                MLD_LAUNCHED("k_var_update");
+            }
+            int s = forward_iters<W>(d, wa, r, d->Lv, t0, t1 - 1, T, slabs, s2, tp, tp->seg_r, tp->seg_lv);
+            if (s != MLD_OK) return s;
+            // r^{t1-1}, L^{t1-1} are now in r / d->Lv; store them as the last segment entry
+            MLD_CUDA(cudaMemcpyAsync(tp->seg_r + (t1 - 1 - t0) * rsz, r, rsz * sizeof(float), cudaMemcpyDeviceToDevice, s2));
+            MLD_CUDA(cudaMemcpyAsync(tp->seg_lv + (t1 - 1 - t0) * lsz, d->Lv, lsz * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, s2));
+            for (int t = t1; t > t0; --t) {
+                const float *rp = tp->seg_r + (t - 1 - t0) * rsz;
+                const float *lvp = tp->seg_lv + (t - 1 - t0) * lsz;
+                if (parts > 0) {
+                    int32_t part0 = 0;
+                    for (const mld::ClassLaunch &cl : classes) {
+                        launch_check_bwd<W>(wa, cl, rp, lvp, tp->gr, t == T ? tp->gd1 : nullptr, tp->gx, tp->glch1,
+                                            tp->gwp, t, slabs, part0, s2);
+                        MLD_LAUNCHED("kw_check_bwd");
+                        part0 += cl.blocks * slabs;
+                    }
+                    kw_reduce_dw<<<1, kReduceThreads, 0, s2>>>(tp->gwp, parts, tp->n_types,
+                                                               tp->dw + static_cast<size_t>(t - 1) * tp->n_types);
+                    MLD_LAUNCHED("kw_reduce_dw");
+                } else {
+                    MLD_CUDA(cudaMemsetAsync(tp->dw + static_cast<size_t>(t - 1) * tp->n_types, 0,
+                                             sizeof(float) * tp->n_types, s2));
+                }
+                if (h.n_core > 0) {
+                    kw_var_bwd<W><<<vgrid, kBlock, 0, s2>>>(wa, tp->gx, tp->glch, t > 1 ? tp->gr : nullptr);
+                    MLD_LAUNCHED("kw_var_bwd");
+                }
             }
         }
-    }
+        return MLD_OK;
+    };
+    int sg = run_graph(d, &tp->bwd_exec, st, segments);
+    if (sg != MLD_OK) return sg;
+    MLD_CUDA(cudaMemcpyAsync(dw, tp->dw, sizeof(float) * T * tp->n_types, cudaMemcpyDeviceToDevice, st));
     if (h.n_vn > 0) {
         kw_deinterleave<W><<<dim3((h.n_vn + 31) / 32, slabs), kBlock, 0, st>>>(
             tp->glch, tp->glch1, d->lch, d->lch1, d->g->unit, h.n_vn, h.n_core, h.n_deg1, tp->batch, d->lmax, dllr);
@@ -677,6 +731,7 @@ int mld_wbp_forward(mld_decoder *d, const float *llr, const uint8_t *syndrome, i
         const size_t lsz = static_cast<size_t>(slabs) * h.n_core * W;
         const size_t dsz = static_cast<size_t>(slabs) * h.n_deg1 * W;
         s = talloc(&tp->w, static_cast<size_t>(T) * n_types);
+        if (s == MLD_OK) s = talloc(&tp->dw, static_cast<size_t>(T) * n_types);
         for (int c = tp->k; s == MLD_OK && c < T; c += tp->k) {
             float *p = nullptr;
             s = talloc(&p, rsz);
